@@ -1,0 +1,228 @@
+/*
+ * ash.h -- C ABI of a GB300 (sm_103a) parallel spatial hash map.
+ *
+ * The operations follow the problem statement of ASH (Dong et al., "ASH: A
+ * Modern Framework for Parallel Spatial Hashing in 3D Perception", arXiv
+ * 2110.00511):
+ *   - Sec. 4.2: an index-first structure-of-arrays map.  A key k is stored at a
+ *     buffer index i of a key buffer kB and of one or more value buffers vB_j
+ *     (Sec. 4.7), and queries return (buffer indices, masks) instead of
+ *     pointers to pairs (the masked query, Eq. (4)).
+ *   - Sec. 4.3: buffer indices come from an index heap h with top t.
+ *   - Sec. 4.3.1: insertion is lazy; a key already present is left untouched.
+ *   - Sec. 5.1: activate inserts keys only and returns their indices.
+ *   - Sec. 1 (footnote on "dynamic" maps): erase.
+ *   - Sec. 4.5: rehash (x2 growth, re-insertion of the active entries).
+ *   - Sec. 4.6: keys are int32 tuples of any dimension 1..8; float keys must be
+ *     quantised first (see ash_quantize, Sec. 6.1).
+ *   - Sec. 4.7: a hash set is a map with zero value buffers.
+ *
+ * Conventions for every call
+ *   - Pointers are DEVICE pointers of the map's device unless the name ends in
+ *     _host.  The caller owns every input and output array; the library owns
+ *     the table, the heap and the key/value buffers.
+ *   - Keys are row-major int32 [n, key_dim] with no padding.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue their kernels on it and return without waiting unless the
+ *     description says "synchronises".
+ *   - Within one batch the FIRST occurrence (lowest position) of a key is the
+ *     one that inserts or erases; later duplicates get mask 0.
+ *   - An output index whose mask is 0 is -1 (the paper leaves it undefined).
+ *   - n = 0 is a valid no-op.  n must be below 2^31 - 1.
+ *   - Return value: ASH_OK or an error code; ash_last_error() gives a message
+ *     for the calling thread.  Errors found by a kernel (a key that could not
+ *     be placed) clear that key's mask, set its index to -1 and are also
+ *     reported by the next synchronising call or by ash_sync_status.
+ */
+#ifndef ASH_H_
+#define ASH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ash_map ash_map;
+/* Same type as cudaStream_t; declared here so this header needs no CUDA headers. */
+typedef struct CUstream_st* ash_stream;
+
+typedef enum ash_status {
+  ASH_OK = 0,
+  ASH_ERR_INVALID = 1,    /* bad argument */
+  ASH_ERR_OOM = 2,        /* device allocation failed */
+  ASH_ERR_CAPACITY = 3,   /* auto-grow off and the index heap ran out */
+  ASH_ERR_TABLE_FULL = 4, /* a key found no free slot within max_probes buckets */
+  ASH_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  ASH_ERR_CUDA = 6        /* any other CUDA error */
+} ash_status;
+
+typedef enum ash_dtype {
+  ASH_F32 = 0, ASH_F16 = 1, ASH_BF16 = 2, ASH_I32 = 3, ASH_I64 = 4, ASH_U8 = 5, ASH_F64 = 6
+} ash_dtype;
+
+/* Layout and launch knobs.  Structural fields (slots_per_bucket,
+ * slots_per_capacity) take effect at create and at the next rehash. */
+typedef struct ash_tuning {
+  int32_t slots_per_bucket;   /* 4, 8 or 16 eight-byte slots: 32, 64 or 128 B buckets */
+  float slots_per_capacity;   /* table slots per unit of capacity (2.0: load <= 0.5) */
+  int32_t block_threads;      /* threads per block of the map kernels (multiple of 32, <= 256) */
+  int32_t blocks_per_sm;      /* grid = SM count x blocks_per_sm (grid-stride loops) */
+  int32_t max_probes;         /* bucket probes before a key fails; 0 = every bucket */
+  int32_t auto_grow;          /* 1: insert/activate double the capacity until size+n <= c (Sec. 4.5) */
+  float max_used_fraction;    /* rebuild the table when live+erased slots would pass this fraction */
+  int32_t inline_value_bytes; /* value rows up to this many bytes (all buffers) are copied by the
+                                 committing thread; larger rows by a warp-per-row scatter kernel */
+} ash_tuning;
+
+/* Fills *out with the defaults. */
+void ash_default_tuning(ash_tuning* out);
+
+/* Optional device allocator used for every buffer the library owns (the table,
+ * key/value buffers, heap, scratch).  alloc returns NULL on failure.  Without
+ * one, the library uses cudaMallocAsync/cudaFreeAsync from the device's
+ * default memory pool on the call's stream.  Applies to maps created after the
+ * call.  Passing NULLs restores the default. */
+typedef void* (*ash_alloc_fn)(size_t bytes, int device, ash_stream stream, void* ctx);
+typedef void (*ash_free_fn)(void* ptr, int device, ash_stream stream, void* ctx);
+ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx);
+
+/* Creates a map on `device` (Sec. 4.2 and 4.7; the constructor of the paper's
+ * HashMap(capacity, key dtype/shape, value dtypes/shapes)).
+ *   key_dim:           1..8 int32 coordinates per key.
+ *   capacity:          c, the maximum number of live entries (heap size),
+ *                      1 <= c and c * slots_per_capacity < 2^31.
+ *   n_values:          0..8 value buffers; 0 makes a hash set.
+ *   value_numel_host:  elements per value row of buffer j (e.g. 512 for 8^3).
+ *   value_dtypes_host: ash_dtype per buffer.
+ *   tuning:            NULL for the defaults.
+ * The key buffer is int32 [c, key_stride] (key_stride = 1, 2, 4 or 8 >= key_dim,
+ * padding zeroed), value buffer j is [c, numel_j] of its dtype, zero-filled.
+ * The table starts empty and the heap as the identity with t = 0. */
+ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t* value_numel_host,
+                      const int32_t* value_dtypes_host, int device, const ash_tuning* tuning,
+                      ash_stream stream, ash_map** out_host);
+
+/* Frees every buffer of the map (on the stream of its last call). */
+ash_status ash_destroy(ash_map* map);
+
+/* Lazy insertion (Sec. 4.3.1) of n keys with their values.
+ *   values_host: host array of n_values device pointers; pointer j addresses
+ *                [n, numel_j] rows of buffer j's dtype.
+ *   buf_indices: int32 [n] out; the new buffer index, or -1.
+ *   masks:       uint8 [n] out; 1 where this position inserted a new key.
+ * A key already in the map, or a later duplicate within the batch, gets mask
+ * 0 and its stored value is not changed.  With auto_grow the capacity first
+ * doubles until size + n <= c (may synchronise). */
+ash_status ash_insert(ash_map* map, const int32_t* keys, const void* const* values_host, int64_t n,
+                      int32_t* buf_indices, uint8_t* masks, ash_stream stream);
+
+/* Activate (Sec. 5.1): insertion of keys only.  Value rows of new entries are
+ * left as they are (zero for never-used indices, stale bytes for indices
+ * re-used after erase).  Outputs as ash_insert. */
+ash_status ash_activate(ash_map* map, const int32_t* keys, int64_t n, int32_t* buf_indices,
+                        uint8_t* masks, ash_stream stream);
+
+/* Masked query (Eq. (4)): mask 1 and the buffer index i with kB(i) = key where
+ * the key is stored; mask 0 and -1 elsewhere. */
+ash_status ash_find(ash_map* map, const int32_t* keys, int64_t n, int32_t* buf_indices,
+                    uint8_t* masks, ash_stream stream);
+
+/* Erase: removes each stored key and returns its buffer index to the heap.
+ *   masks: uint8 [n] out; 1 at the first position of each key that was
+ *          stored, 0 elsewhere.
+ * Uses n * 4 bytes of library-owned scratch (grown on demand). */
+ash_status ash_erase(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
+
+/* Lists the buffer indices of all live entries (the "active" entries that
+ * Sec. 4.5 collects for rehash).  Order unspecified.  Writes at most
+ * out_capacity indices to out and the live count to *count_host.
+ * Synchronises the stream. */
+ash_status ash_get_active_indices(ash_map* map, int32_t* out, int64_t out_capacity,
+                                  int64_t* count_host, ash_stream stream);
+
+/* Number of live entries (the heap top t).  Synchronises the stream. */
+ash_status ash_size(ash_map* map, int64_t* size_host, ash_stream stream);
+
+/* Capacity c, key dimension, and value-buffer count. */
+int64_t ash_capacity(const ash_map* map);
+int ash_key_dim(const ash_map* map);
+int ash_n_values(const ash_map* map);
+
+/* Rehash (Sec. 4.5) to new_capacity (0 = 2c).  new_capacity must be >= the
+ * live count.  When new_capacity >= c the live entries keep their buffer
+ * indices (buffers grow, the table is rebuilt); below c they are renumbered
+ * 0..size-1.  Invalidates pointers from ash_key_buffer / ash_value_buffer.
+ * Synchronises the stream. */
+ash_status ash_rehash(ash_map* map, int64_t new_capacity, ash_stream stream);
+
+/* Grows the capacity to at least new_capacity (no-op if already there). */
+ash_status ash_reserve(ash_map* map, int64_t new_capacity, ash_stream stream);
+
+/* Removes every entry: empty table, identity heap, t = 0.  Value bytes stay. */
+ash_status ash_clear(ash_map* map, ash_stream stream);
+
+/* The key buffer kB (int32 [c, *row_stride]) and value buffer vB_j
+ * ([c, numel_j], *row_bytes per row).  Device pointers owned by the map; valid
+ * until the next rehash, reserve, growth or destroy. */
+ash_status ash_key_buffer(ash_map* map, int32_t** ptr_host, int64_t* row_stride_host);
+ash_status ash_value_buffer(ash_map* map, int j, void** ptr_host, int64_t* row_bytes_host);
+
+/* The index heap h (int32 [c]) and a device pointer to its top t (int32, the
+ * low word of the map's control word).  For invariant checks. */
+ash_status ash_heap_buffer(ash_map* map, int32_t** heap_host, int32_t** top_host);
+
+/* Gathers key rows: out[r, 0:key_dim] = kB(indices[r]); rows whose index is
+ * outside [0, c) are written as zeros.  out is int32 [n, key_dim]. */
+ash_status ash_gather_keys(ash_map* map, const int32_t* indices, int64_t n, int32_t* out,
+                           ash_stream stream);
+
+ash_status ash_get_tuning(const ash_map* map, ash_tuning* out_host);
+ash_status ash_set_tuning(ash_map* map, const ash_tuning* tuning_host);
+
+/* Synchronises the stream and returns (then clears) the first error that a
+ * kernel of this map reported since the last check. */
+ash_status ash_sync_status(ash_map* map, ash_stream stream);
+
+/* Voxel quantisation (Sec. 6.1 listing; Eq. (10) with s*l as the cell edge):
+ * keys[j] = floor(points[j] / cell) per coordinate, computed in float32 with
+ * IEEE division and rounding toward minus infinity, for n_coords floats.
+ * Quotients outside the int32 range saturate.  cell must be finite and > 0. */
+ash_status ash_quantize(const float* points, int64_t n_coords, float cell, int32_t* keys,
+                        ash_stream stream);
+
+/* Random-sector read probe (measurement only, not part of the map): n_reads
+ * reads of sector_bytes (32 or 64) at pseudo-random sector-aligned offsets of
+ * buf (buf_bytes, multiple of 64), XOR-folded into sink[0..grid).  Sets the
+ * random-access roofline the map kernels are compared with. */
+ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_reads,
+                                 int sector_bytes, uint32_t seed, uint32_t* sink, int64_t sink_len,
+                                 ash_stream stream);
+
+/* Kernel tracing (measurement support, not part of the map).  The library
+ * counts every kernel it launches; with tracing on it also records a CUDA
+ * event pair around each launch on the launching stream.
+ *   ash_trace_kernel_kinds / ash_trace_kernel_name: the kernel kinds.
+ *   ash_trace_enable(1/0): start / stop recording events.
+ *   ash_trace_collect: waits for the recorded events and adds their elapsed
+ *     times to per-kind totals (synchronises on those events).
+ *   ash_trace_read: total milliseconds and timed launches of one kind.
+ *   ash_trace_reset: zeroes the totals.
+ *   ash_kernel_launch_count: kernels launched by this library since load. */
+int ash_trace_kernel_kinds(void);
+const char* ash_trace_kernel_name(int kind);
+ash_status ash_trace_enable(int on);
+ash_status ash_trace_collect(void);
+ash_status ash_trace_read(int kind, double* total_ms_host, int64_t* launches_host);
+ash_status ash_trace_reset(void);
+uint64_t ash_kernel_launch_count(void);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* ash_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASH_H_ */

@@ -1,0 +1,424 @@
+"""Thin ctypes binding of libash.so (include/ash.h).
+
+Functions named ash_* mirror the C ABI one to one and only marshal torch
+tensors (device pointers, sizes, the current CUDA stream).  Every step of the
+hash map runs in the library's CUDA kernels; there is no CPU fallback: if
+libash.so is missing or no GPU is present, calls raise.
+
+`HashMap` wraps one map with the interface of the paper's HashMap (Sec. 4.2,
+listings of Sec. 6): insert / activate / find return (buf_indices, masks);
+value and key buffers are exposed as zero-copy tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libash.so")
+
+ASH_OK, ASH_ERR_INVALID, ASH_ERR_OOM, ASH_ERR_CAPACITY, ASH_ERR_TABLE_FULL, ASH_ERR_TIMEOUT, ASH_ERR_CUDA = range(7)
+_STATUS_NAMES = ["ASH_OK", "ASH_ERR_INVALID", "ASH_ERR_OOM", "ASH_ERR_CAPACITY", "ASH_ERR_TABLE_FULL",
+                 "ASH_ERR_TIMEOUT", "ASH_ERR_CUDA"]
+
+DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2, torch.int32: 3, torch.int64: 4,
+          torch.uint8: 5, torch.float64: 6}
+
+
+class AshError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("slots_per_bucket", ctypes.c_int32), ("slots_per_capacity", ctypes.c_float),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("max_probes", ctypes.c_int32), ("auto_grow", ctypes.c_int32),
+                ("max_used_fraction", ctypes.c_float), ("inline_value_bytes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_lib = None
+
+# C signatures: name -> (restype, argtypes)
+_SIGS = {
+    "ash_default_tuning": (None, [ctypes.POINTER(Tuning)]),
+    "ash_set_allocator": (_I32, [_P, _P, _P]),
+    "ash_create": (_I32, [ctypes.c_int, _I64, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.c_int,
+                          ctypes.POINTER(Tuning), _P, ctypes.POINTER(_P)]),
+    "ash_destroy": (_I32, [_P]),
+    "ash_insert": (_I32, [_P, _P, ctypes.POINTER(_P), _I64, _P, _P, _P]),
+    "ash_activate": (_I32, [_P, _P, _I64, _P, _P, _P]),
+    "ash_find": (_I32, [_P, _P, _I64, _P, _P, _P]),
+    "ash_erase": (_I32, [_P, _P, _I64, _P, _P]),
+    "ash_get_active_indices": (_I32, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "ash_size": (_I32, [_P, ctypes.POINTER(_I64), _P]),
+    "ash_capacity": (_I64, [_P]),
+    "ash_key_dim": (ctypes.c_int, [_P]),
+    "ash_n_values": (ctypes.c_int, [_P]),
+    "ash_rehash": (_I32, [_P, _I64, _P]),
+    "ash_reserve": (_I32, [_P, _I64, _P]),
+    "ash_clear": (_I32, [_P, _P]),
+    "ash_key_buffer": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "ash_value_buffer": (_I32, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "ash_heap_buffer": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "ash_gather_keys": (_I32, [_P, _P, _I64, _P, _P]),
+    "ash_get_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
+    "ash_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
+    "ash_sync_status": (_I32, [_P, _P]),
+    "ash_quantize": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
+    "ash_probe_random_read": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
+    "ash_trace_kernel_kinds": (ctypes.c_int, []),
+    "ash_trace_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "ash_trace_enable": (_I32, [ctypes.c_int]),
+    "ash_trace_collect": (_I32, []),
+    "ash_trace_read": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "ash_trace_reset": (_I32, []),
+    "ash_kernel_launch_count": (ctypes.c_uint64, []),
+    "ash_last_error": (ctypes.c_char_p, []),
+}
+
+
+def exported_symbols():
+    """Names the binding expects libash.so to export."""
+    return list(_SIGS)
+
+
+def lib():
+    """Loads libash.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libash.so is not built ({LIB_PATH}); run paper_2110_00511_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ASH_OK:
+        raise AshError(status, lib().ash_last_error().decode())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need_cuda(t, name, dtype=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ shim for zero-copy tensor views of library buffers."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+_TYPESTR = {torch.float32: "<f4", torch.float16: "<f2", torch.int32: "<i4", torch.int64: "<i8",
+            torch.uint8: "|u1", torch.float64: "<f8"}
+
+
+def _view(ptr, shape, dtype, device, owner):
+    if dtype == torch.bfloat16:
+        raw = torch.as_tensor(_DeviceArray(ptr, shape, "<i2", owner), device=device)
+        return raw.view(torch.bfloat16)
+    return torch.as_tensor(_DeviceArray(ptr, shape, _TYPESTR[dtype], owner), device=device)
+
+
+def default_tuning() -> Tuning:
+    t = Tuning()
+    lib().ash_default_tuning(ctypes.byref(t))
+    return t
+
+
+# ------------------------------------------------------------ allocator hook
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_alloc_keepalive = []
+
+
+def use_torch_allocator(enable: bool = True):
+    """Routes the library's device allocations through PyTorch's caching
+    allocator (maps created afterwards).  Off: cudaMallocAsync pool."""
+    if not enable:
+        _check(lib().ash_set_allocator(None, None, None))
+        _alloc_keepalive.clear()
+        return
+
+    def _alloc(nbytes, device, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:
+            return 0
+
+    def _free(ptr, device, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _alloc_keepalive[:] = [a, f]
+    _check(lib().ash_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+
+
+# ---------------------------------------------------------------- functions
+def ash_create(key_dim, capacity, value_numel=(), value_dtypes=(), device=0, tuning=None, stream=None):
+    n_values = len(value_numel)
+    numel = (_I64 * max(1, n_values))(*[int(x) for x in value_numel])
+    dts = (_I32 * max(1, n_values))(*[DTYPES[d] if isinstance(d, torch.dtype) else int(d) for d in value_dtypes])
+    out = ctypes.c_void_p()
+    _check(lib().ash_create(int(key_dim), int(capacity), n_values, numel, dts, int(device),
+                            ctypes.byref(tuning) if tuning is not None else None,
+                            stream if stream is not None else _stream(device), ctypes.byref(out)))
+    return out
+
+
+def ash_destroy(handle):
+    _check(lib().ash_destroy(handle))
+
+
+def ash_insert(handle, keys, values, buf_indices, masks, stream=None):
+    arr = (ctypes.c_void_p * max(1, len(values)))(*[v.data_ptr() for v in values])
+    _check(lib().ash_insert(handle, _ptr(keys), arr, keys.shape[0], _ptr(buf_indices), _ptr(masks),
+                            stream if stream is not None else _stream(keys.device)))
+
+
+def ash_activate(handle, keys, buf_indices, masks, stream=None):
+    _check(lib().ash_activate(handle, _ptr(keys), keys.shape[0], _ptr(buf_indices), _ptr(masks),
+                              stream if stream is not None else _stream(keys.device)))
+
+
+def ash_find(handle, keys, buf_indices, masks, stream=None):
+    _check(lib().ash_find(handle, _ptr(keys), keys.shape[0], _ptr(buf_indices), _ptr(masks),
+                          stream if stream is not None else _stream(keys.device)))
+
+
+def ash_erase(handle, keys, masks, stream=None):
+    _check(lib().ash_erase(handle, _ptr(keys), keys.shape[0], _ptr(masks),
+                           stream if stream is not None else _stream(keys.device)))
+
+
+def ash_get_active_indices(handle, out, stream=None):
+    count = _I64()
+    _check(lib().ash_get_active_indices(handle, _ptr(out), out.numel(), ctypes.byref(count),
+                                        stream if stream is not None else _stream(out.device)))
+    return int(count.value)
+
+
+def ash_size(handle, stream=None):
+    v = _I64()
+    _check(lib().ash_size(handle, ctypes.byref(v), stream if stream is not None else _stream()))
+    return int(v.value)
+
+
+def ash_rehash(handle, new_capacity=0, stream=None):
+    _check(lib().ash_rehash(handle, int(new_capacity), stream if stream is not None else _stream()))
+
+
+def ash_reserve(handle, new_capacity, stream=None):
+    _check(lib().ash_reserve(handle, int(new_capacity), stream if stream is not None else _stream()))
+
+
+def ash_clear(handle, stream=None):
+    _check(lib().ash_clear(handle, stream if stream is not None else _stream()))
+
+
+def ash_gather_keys(handle, indices, out, stream=None):
+    _check(lib().ash_gather_keys(handle, _ptr(indices), indices.numel(), _ptr(out),
+                                 stream if stream is not None else _stream(indices.device)))
+
+
+def ash_sync_status(handle, stream=None):
+    _check(lib().ash_sync_status(handle, stream if stream is not None else _stream()))
+
+
+def ash_quantize(points, cell, out=None, stream=None):
+    """int32 keys floor(points / cell) (Sec. 6.1), same shape as points."""
+    _need_cuda(points, "points", torch.float32)
+    if out is None:
+        out = torch.empty(points.shape, dtype=torch.int32, device=points.device)
+    _check(lib().ash_quantize(_ptr(points), points.numel(), ctypes.c_float(cell), _ptr(out),
+                              stream if stream is not None else _stream(points.device)))
+    return out
+
+
+def ash_probe_random_read(buf, n_reads, sector_bytes, sink, seed=0, stream=None):
+    _check(lib().ash_probe_random_read(_ptr(buf), buf.numel() * buf.element_size(), int(n_reads), int(sector_bytes),
+                                       ctypes.c_uint32(seed), _ptr(sink), sink.numel(),
+                                       stream if stream is not None else _stream(buf.device)))
+
+
+def ash_trace_enable(on=True):
+    _check(lib().ash_trace_enable(1 if on else 0))
+
+
+def ash_trace_reset():
+    _check(lib().ash_trace_reset())
+
+
+def ash_trace_collect():
+    """{kernel kind: (total ms, timed launches)} after waiting for the events."""
+    L = lib()
+    _check(L.ash_trace_collect())
+    out = {}
+    for k in range(L.ash_trace_kernel_kinds()):
+        ms, n = ctypes.c_double(), _I64()
+        _check(L.ash_trace_read(k, ctypes.byref(ms), ctypes.byref(n)))
+        out[L.ash_trace_kernel_name(k).decode()] = (ms.value, int(n.value))
+    return out
+
+
+def ash_kernel_launch_count():
+    return int(lib().ash_kernel_launch_count())
+
+
+# -------------------------------------------------------------------- class
+class HashMap:
+    """A GPU hash map with int32 keys of dimension key_dim and SoA value
+    buffers (Sec. 4.2, 4.7).  value_shapes=() makes a hash set."""
+
+    def __init__(self, key_dim, capacity, value_shapes=(), value_dtypes=(), device=None, tuning=None):
+        if len(value_shapes) != len(value_dtypes):
+            raise ValueError("value_shapes and value_dtypes differ in length")
+        if not torch.cuda.is_available():
+            raise RuntimeError("HashMap needs a CUDA device (there is no CPU fallback)")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        self.key_dim = int(key_dim)
+        self.value_shapes = [tuple(int(x) for x in (s if isinstance(s, (tuple, list)) else (s,))) for s in value_shapes]
+        self.value_dtypes = list(value_dtypes)
+        numel = [int(torch.Size(s).numel()) for s in self.value_shapes]
+        self._h = ash_create(self.key_dim, capacity, numel, self.value_dtypes, self.device.index, tuning,
+                             _stream(self.device))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().ash_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def _keys(self, keys):
+        _need_cuda(keys, "keys", torch.int32)
+        if keys.dim() != 2 or keys.shape[1] != self.key_dim:
+            raise ValueError(f"keys must be int32 [N, {self.key_dim}]")
+        return keys
+
+    def _outputs(self, n):
+        return (torch.empty(n, dtype=torch.int32, device=self.device),
+                torch.empty(n, dtype=torch.bool, device=self.device))
+
+    def insert(self, keys, values):
+        keys = self._keys(keys)
+        values = list(values) if isinstance(values, (list, tuple)) else [values]
+        if len(values) != len(self.value_shapes):
+            raise ValueError("one value tensor per value buffer is required")
+        for v, shp, dt in zip(values, self.value_shapes, self.value_dtypes):
+            _need_cuda(v, "values", dt)
+            if v.numel() != keys.shape[0] * torch.Size(shp).numel():
+                raise ValueError("value tensor does not match [N, *shape]")
+        idx, mask = self._outputs(keys.shape[0])
+        ash_insert(self._h, keys, values, idx, mask)
+        return idx, mask
+
+    def activate(self, keys):
+        keys = self._keys(keys)
+        idx, mask = self._outputs(keys.shape[0])
+        ash_activate(self._h, keys, idx, mask)
+        return idx, mask
+
+    def find(self, keys):
+        keys = self._keys(keys)
+        idx, mask = self._outputs(keys.shape[0])
+        ash_find(self._h, keys, idx, mask)
+        return idx, mask
+
+    def erase(self, keys):
+        keys = self._keys(keys)
+        mask = torch.empty(keys.shape[0], dtype=torch.bool, device=self.device)
+        ash_erase(self._h, keys, mask)
+        return mask
+
+    def active_indices(self):
+        out = torch.empty(max(1, self.capacity()), dtype=torch.int32, device=self.device)
+        n = ash_get_active_indices(self._h, out)
+        return out[:n]
+
+    def size(self):
+        return ash_size(self._h, _stream(self.device))
+
+    def capacity(self):
+        return int(lib().ash_capacity(self._h))
+
+    def rehash(self, new_capacity=0):
+        ash_rehash(self._h, new_capacity, _stream(self.device))
+
+    def reserve(self, new_capacity):
+        ash_reserve(self._h, new_capacity, _stream(self.device))
+
+    def clear(self):
+        ash_clear(self._h, _stream(self.device))
+
+    def sync_status(self):
+        ash_sync_status(self._h, _stream(self.device))
+
+    def gather_keys(self, indices):
+        out = torch.empty((indices.numel(), self.key_dim), dtype=torch.int32, device=self.device)
+        ash_gather_keys(self._h, indices.to(torch.int32).contiguous(), out)
+        return out
+
+    def key_buffer(self):
+        """int32 [capacity, key_dim] view of kB (valid until the next rehash)."""
+        p, stride = ctypes.c_void_p(), _I64()
+        _check(lib().ash_key_buffer(self._h, ctypes.byref(p), ctypes.byref(stride)))
+        full = _view(p.value, (self.capacity(), stride.value), torch.int32, self.device, self)
+        return full[:, : self.key_dim]
+
+    def value_buffer(self, j=0):
+        """[capacity, *shape_j] view of vB_j (valid until the next rehash)."""
+        p, rb = ctypes.c_void_p(), _I64()
+        _check(lib().ash_value_buffer(self._h, j, ctypes.byref(p), ctypes.byref(rb)))
+        return _view(p.value, (self.capacity(), *self.value_shapes[j]), self.value_dtypes[j], self.device, self)
+
+    def heap(self):
+        """(h as int32 [capacity] view, heap top t)."""
+        hp, tp = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().ash_heap_buffer(self._h, ctypes.byref(hp), ctypes.byref(tp)))
+        h = _view(hp.value, (self.capacity(),), torch.int32, self.device, self)
+        t = _view(tp.value, (1,), torch.int32, self.device, self)
+        return h, int(t.item())
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().ash_get_tuning(self._h, ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, t):
+        _check(lib().ash_set_tuning(self._h, ctypes.byref(t)))
+
+    @property
+    def handle(self):
+        return self._h

@@ -1,0 +1,260 @@
+// Map kernels that do not depend on the key dimension: erase resolve, the
+// active-index listing, heap initialisation, value-row scatter/gather, key
+// gather, voxel quantisation and the random-read roofline probe.
+#include "ash_aux.h"
+#include "ash_kernels.cuh"
+#include "ash_trace.h"
+
+namespace ash {
+
+// ------------------------------------------------------------ erase resolve
+template <int S>
+static void erase_resolve_s(const TableView& t, int64_t n, const int32_t* slot_in, uint8_t* mask, const Launch& L) {
+  TraceScope ts(kKEraseResolve, L.stream);
+  erase_resolve_kernel<S><<<grid_for(n, L), L.block, 0, L.stream>>>(t, n, slot_in, mask);
+}
+
+void launch_erase_resolve(int S, const TableView& t, int64_t n, const int32_t* slot_in, uint8_t* mask, const Launch& L) {
+  if (S == 4) erase_resolve_s<4>(t, n, slot_in, mask, L);
+  else if (S == 8) erase_resolve_s<8>(t, n, slot_in, mask, L);
+  else erase_resolve_s<16>(t, n, slot_in, mask, L);
+}
+
+// ----------------------------------------------------------- active listing
+// Block-wide exclusive scan of a small per-thread count.
+__device__ __forceinline__ int block_exclusive_scan(int v, int& total, int* s_warp) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int n_warps = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < n_warps; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = acc;
+      acc += c;
+    }
+    s_warp[n_warps] = acc;
+  }
+  __syncthreads();
+  total = s_warp[n_warps];
+  return s_warp[warp] + x - v;
+}
+
+// Each thread reads one 32-byte group of 4 slots; committed slots (low word
+// below kClaimBit) contribute their buffer index.  One atomic per block
+// reserves the output range.
+__global__ void __launch_bounds__(256) list_active_kernel(const uint64_t* __restrict__ slots, int64_t n_groups,
+                                                          Ctrl* ctrl, int32_t* __restrict__ out, int64_t out_cap) {
+  __shared__ int s_warp[33];
+  __shared__ unsigned long long s_base;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n_groups; base += stride) {
+    const int64_t g = base + threadIdx.x;
+    uint64_t w[4] = {kEmpty, kEmpty, kEmpty, kEmpty};
+    if (g < n_groups) load32<true>(slots + 4 * g, w[0], w[1], w[2], w[3]);
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c += (lo32(w[q]) < kClaimBit) ? 1 : 0;
+    int total;
+    const int off = block_exclusive_scan(c, total, s_warp);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctrl->count, static_cast<unsigned long long>(total)) : 0ull;
+    __syncthreads();
+    int64_t o = static_cast<int64_t>(s_base) + off;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (lo32(w[q]) < kClaimBit) {
+        if (o < out_cap) out[o] = static_cast<int32_t>(lo32(w[q]));
+        ++o;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_list_active(const uint64_t* slots, int64_t n_slots, Ctrl* ctrl, int32_t* out, int64_t out_cap,
+                        const Launch& L) {
+  const int64_t groups = n_slots / 4;
+  TraceScope ts(kKListActive, L.stream);
+  list_active_kernel<<<grid_for(groups, L), L.block, 0, L.stream>>>(slots, groups, ctrl, out, out_cap);
+}
+
+// ------------------------------------------------------------------- heap
+__global__ void iota_kernel(int32_t* __restrict__ h, int64_t from, int64_t to) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = from + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < to; i += stride)
+    h[i] = static_cast<int32_t>(i);
+}
+
+void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L) {
+  if (to <= from) return;
+  TraceScope ts(kKIota, L.stream);
+  iota_kernel<<<grid_for(to - from, L), L.block, 0, L.stream>>>(h, from, to);
+}
+
+__global__ void set_top_used_kernel(Ctrl* ctrl, unsigned long long top_used) { ctrl->top_used = top_used; }
+
+void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L) {
+  const unsigned long long v = (static_cast<unsigned long long>(used) << 32) | static_cast<unsigned long long>(top);
+  TraceScope ts(kKSetCtrl, L.stream);
+  set_top_used_kernel<<<1, 1, 0, L.stream>>>(ctrl, v);
+}
+
+// -------------------------------------------------------------- value rows
+// Warp per input position: rows of winners (mask[p] == 1) are copied from
+// src_j + p*row to dst_j + idx[p]*row, 32 lanes x vec bytes per step.
+__global__ void __launch_bounds__(256) scatter_rows_kernel(ValueCopy vc, const int32_t* __restrict__ idx,
+                                                           const uint8_t* __restrict__ mask, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
+    if (!mask[p]) continue;
+    const int64_t i = idx[p];
+#pragma unroll
+    for (int j = 0; j < kMaxValues; ++j) {
+      if (j < vc.n)
+        copy_row(static_cast<char*>(vc.dst[j]) + i * vc.row_bytes[j],
+                 static_cast<const char*>(vc.src[j]) + p * vc.row_bytes[j], vc.row_bytes[j], vc.vec[j], lane, 32);
+    }
+  }
+}
+
+void launch_scatter_rows(const ValueCopy& vc, const int32_t* idx, const uint8_t* mask, int64_t n, const Launch& L) {
+  if (vc.n == 0 || n == 0) return;
+  int64_t g = (n * 32 + L.block - 1) / L.block;
+  if (g > L.grid_cap) g = L.grid_cap;
+  TraceScope ts(kKScatterRows, L.stream);
+  scatter_rows_kernel<<<static_cast<int>(g < 1 ? 1 : g), L.block, 0, L.stream>>>(vc, idx, mask, n);
+}
+
+// Warp per row: dst_j row r <- src_j row list[r] (compacting rehash).
+__global__ void __launch_bounds__(256) gather_rows_kernel(ValueCopy vc, const int32_t* __restrict__ list, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const int64_t a = list[r];
+#pragma unroll
+    for (int j = 0; j < kMaxValues; ++j) {
+      if (j < vc.n)
+        copy_row(static_cast<char*>(vc.dst[j]) + r * vc.row_bytes[j],
+                 static_cast<const char*>(vc.src[j]) + a * vc.row_bytes[j], vc.row_bytes[j], vc.vec[j], lane, 32);
+    }
+  }
+}
+
+void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, const Launch& L) {
+  if (vc.n == 0 || n == 0) return;
+  int64_t g = (n * 32 + L.block - 1) / L.block;
+  if (g > L.grid_cap) g = L.grid_cap;
+  TraceScope ts(kKGatherRows, L.stream);
+  gather_rows_kernel<<<static_cast<int>(g < 1 ? 1 : g), L.block, 0, L.stream>>>(vc, list, n);
+}
+
+// --------------------------------------------------------------- key gather
+__global__ void gather_keys_kernel(const int32_t* __restrict__ kb, int ks, int d, int64_t capacity,
+                                   const int32_t* __restrict__ indices, int64_t n, int32_t* __restrict__ out) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n * d; e += stride) {
+    const int64_t r = e / d;
+    const int c = static_cast<int>(e - r * d);
+    const int32_t i = indices[r];
+    out[e] = (i >= 0 && i < capacity) ? kb[static_cast<int64_t>(i) * ks + c] : 0;
+  }
+}
+
+void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, const int32_t* indices, int64_t n,
+                        int32_t* out, const Launch& L) {
+  if (n == 0) return;
+  TraceScope ts(kKGatherKeys, L.stream);
+  gather_keys_kernel<<<grid_for(n * d, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, out);
+}
+
+// ------------------------------------------------------------- quantisation
+// floor(p / cell) in float32 with IEEE division (this file is compiled without
+// fast-math), then float -> int32 conversion rounding toward minus infinity
+// (saturating outside the int32 range).
+__global__ void quantize_kernel(const float* __restrict__ pts, int64_t n, int64_t n4, float cell,
+                                int32_t* __restrict__ keys) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const float4* p4 = reinterpret_cast<const float4*>(pts);
+  int4* k4 = reinterpret_cast<int4*>(keys);
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 v = __ldcs(p4 + i);
+    int4 o;
+    o.x = __float2int_rd(__fdiv_rn(v.x, cell));
+    o.y = __float2int_rd(__fdiv_rn(v.y, cell));
+    o.z = __float2int_rd(__fdiv_rn(v.z, cell));
+    o.w = __float2int_rd(__fdiv_rn(v.w, cell));
+    __stcs(k4 + i, o);
+  }
+  for (int64_t i = 4 * n4 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    keys[i] = __float2int_rd(__fdiv_rn(pts[i], cell));
+}
+
+void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L) {
+  if (n == 0) return;
+  // the float4 path needs both arrays 16-byte aligned
+  const bool vec_ok = ((reinterpret_cast<uintptr_t>(pts) | reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
+  const int64_t n4 = vec_ok ? n / 4 : 0;
+  TraceScope ts(kKQuantize, L.stream);
+  quantize_kernel<<<grid_for((n + 3) / 4, L), L.block, 0, L.stream>>>(pts, n, n4, cell, keys);
+}
+
+// ----------------------------------------------------------- roofline probe
+// Each thread performs reads at pseudo-random sector-aligned offsets (a
+// splitmix64 sequence), XOR-folds them and writes one word per block, so the
+// loads cannot be removed.  Several independent reads are in flight per
+// thread.
+template <int SECTOR>
+__global__ void __launch_bounds__(256) probe_kernel(const uint64_t* __restrict__ buf, uint64_t n_sectors,
+                                                    int64_t n_reads, uint32_t seed, uint32_t* __restrict__ sink,
+                                                    int64_t sink_len) {
+  constexpr int UNROLL = 4;
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  uint64_t acc = 0;
+  for (int64_t r0 = tid * UNROLL; r0 < n_reads; r0 += nthreads * UNROLL) {
+    uint64_t v[UNROLL][4];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int64_t r = r0 + u;
+      const uint64_t sec = __umul64hi(mix64(static_cast<uint64_t>(r) * 0x9E3779B97F4A7C15ull + seed), n_sectors);
+      const uint64_t* p = buf + sec * (SECTOR / 8);
+      if (r < n_reads) {
+        load32<true>(p, v[u][0], v[u][1], v[u][2], v[u][3]);
+        if constexpr (SECTOR == 64) {
+          uint64_t a, b, c, d;
+          load32<true>(p + 4, a, b, c, d);
+          v[u][0] ^= a; v[u][1] ^= b; v[u][2] ^= c; v[u][3] ^= d;
+        }
+      } else {
+        v[u][0] = v[u][1] = v[u][2] = v[u][3] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) acc ^= v[u][0] ^ v[u][1] ^ v[u][2] ^ v[u][3];
+  }
+  const uint32_t folded = static_cast<uint32_t>(acc ^ (acc >> 32));
+  const int64_t slot = tid % sink_len;
+  if (folded == 0x9E3779B9u) sink[slot] = folded;  // practically never taken; keeps the loads live
+}
+
+void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
+                  int64_t sink_len, const Launch& L) {
+  const uint64_t n_sectors = static_cast<uint64_t>(buf_bytes) / static_cast<uint64_t>(sector);
+  const int grid = L.grid_cap;
+  TraceScope ts(kKProbe, L.stream);
+  if (sector == 64)
+    probe_kernel<64><<<grid, L.block, 0, L.stream>>>(static_cast<const uint64_t*>(buf), n_sectors, n_reads, seed, sink, sink_len);
+  else
+    probe_kernel<32><<<grid, L.block, 0, L.stream>>>(static_cast<const uint64_t*>(buf), n_sectors, n_reads, seed, sink, sink_len);
+}
+
+}  // namespace ash

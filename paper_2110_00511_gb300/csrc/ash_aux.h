@@ -1,0 +1,25 @@
+// Host-side launchers of the dimension-independent kernels (ash_aux.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ash_device.cuh"
+
+namespace ash {
+
+struct Launch;
+
+void launch_list_active(const uint64_t* slots, int64_t n_slots, Ctrl* ctrl, int32_t* out, int64_t out_cap,
+                        const Launch& L);
+void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L);
+void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);
+void launch_scatter_rows(const ValueCopy& vc, const int32_t* idx, const uint8_t* mask, int64_t n, const Launch& L);
+void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, const Launch& L);
+void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, const int32_t* indices, int64_t n,
+                        int32_t* out, const Launch& L);
+void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L);
+void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
+                  int64_t sink_len, const Launch& L);
+
+}  // namespace ash

@@ -1,0 +1,756 @@
+// Host side of the hash map and the C ABI declared in include/ash.h.
+//
+// The map object owns the table, the key buffer kB, the value buffers vB_j,
+// the index heap h and a small control block (heap top t, used slots, error
+// bits) in device memory.  Every operation is a short sequence of kernel
+// launches on the caller's stream; the host synchronises only where the
+// answer is needed on the host (size, listing, rehash) or when the host-side
+// upper bounds on the live and used counts say that the batch might not fit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ash.h"
+#include "ash_aux.h"
+#include "ash_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ash_status fail(ash_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ash_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ASH_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ASH_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+struct Allocator {
+  ash_alloc_fn alloc = nullptr;
+  ash_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+
+std::mutex g_mu;
+Allocator g_alloc;
+bool g_pool_ready[64] = {};
+
+int64_t dtype_bytes(int32_t dt) {
+  switch (dt) {
+    case ASH_F32: case ASH_I32: return 4;
+    case ASH_F16: case ASH_BF16: return 2;
+    case ASH_I64: case ASH_F64: return 8;
+    case ASH_U8: return 1;
+    default: return 0;
+  }
+}
+
+int sm_count(int device) {
+  static int cache[64] = {};
+  if (device < 0 || device >= 64) return 1;
+  if (cache[device] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    cache[device] = v > 0 ? v : 1;
+  }
+  return cache[device];
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int vec_width(int64_t row_bytes, const void* a, const void* b) {
+  const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b);
+  for (int v : {16, 8, 4, 2}) {
+    if (row_bytes % v == 0 && (al % v) == 0) return v;
+  }
+  return 1;
+}
+
+}  // namespace
+
+struct ash_map {
+  int device = 0;
+  int key_dim = 0;
+  int ks = 0;  // key stride in kB
+  int n_values = 0;
+  int64_t capacity = 0;
+  int64_t n_slots = 0;
+  uint32_t n_buckets = 0;
+  int S = 4;
+  std::vector<int64_t> numel;
+  std::vector<int32_t> dtype;
+  std::vector<int64_t> row_bytes;
+  uint64_t* slots = nullptr;
+  int32_t* kb = nullptr;
+  int32_t* heap = nullptr;
+  std::vector<void*> vb;
+  ash::Ctrl* ctrl = nullptr;
+  ash::Ctrl* ctrl_host = nullptr;  // pinned mirror for synchronising reads
+  int32_t* scratch = nullptr;
+  int64_t scratch_bytes = 0;
+  int64_t size_ub = 0;  // upper bound of live entries since the last sync
+  int64_t used_ub = 0;  // upper bound of used slots since the last sync
+  ash_tuning tuning{};
+  ash::DimKernels K{};
+  Allocator alloc;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void* dev_alloc(ash_map* m, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 256;
+  if (m->alloc.alloc) return m->alloc.alloc(bytes, m->device, reinterpret_cast<ash_stream>(st), m->alloc.ctx);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (m->device >= 0 && m->device < 64 && !g_pool_ready[m->device]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, m->device) == cudaSuccess) {
+        uint64_t keep = ~0ull;  // cache freed blocks in this process's pool
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      g_pool_ready[m->device] = true;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(ash_map* m, void* p, cudaStream_t st) {
+  if (!p) return;
+  if (m->alloc.free) {
+    m->alloc.free(p, m->device, reinterpret_cast<ash_stream>(st), m->alloc.ctx);
+    return;
+  }
+  cudaFreeAsync(p, st);
+}
+
+ash::DimKernels kernels_for(int d) {
+  switch (d) {
+    case 1: return ash::dim_kernels_1();
+    case 2: return ash::dim_kernels_2();
+    case 3: return ash::dim_kernels_3();
+    case 4: return ash::dim_kernels_4();
+    case 5: return ash::dim_kernels_5();
+    case 6: return ash::dim_kernels_6();
+    case 7: return ash::dim_kernels_7();
+    default: return ash::dim_kernels_8();
+  }
+}
+
+ash::Launch launch_of(const ash_map* m, cudaStream_t st) {
+  ash::Launch L;
+  L.stream = st;
+  L.block = m->tuning.block_threads;
+  L.grid_cap = sm_count(m->device) * m->tuning.blocks_per_sm;
+  return L;
+}
+
+ash::TableView view_of(const ash_map* m) {
+  ash::TableView t;
+  t.slots = m->slots;
+  t.kb = m->kb;
+  t.heap = m->heap;
+  t.ctrl = m->ctrl;
+  t.n_buckets = m->n_buckets;
+  t.max_probes = (m->tuning.max_probes > 0 && static_cast<uint32_t>(m->tuning.max_probes) < m->n_buckets)
+                     ? static_cast<uint32_t>(m->tuning.max_probes)
+                     : m->n_buckets;
+  t.capacity = static_cast<int32_t>(m->capacity);
+  t.pad = 0;
+  return t;
+}
+
+ash_status validate_tuning(const ash_tuning& t) {
+  if (t.slots_per_bucket != 4 && t.slots_per_bucket != 8 && t.slots_per_bucket != 16)
+    return fail(ASH_ERR_INVALID, "slots_per_bucket must be 4, 8 or 16");
+  if (!(t.slots_per_capacity >= 1.05f && t.slots_per_capacity <= 64.0f))
+    return fail(ASH_ERR_INVALID, "slots_per_capacity must be in [1.05, 64]");
+  if (t.block_threads < 32 || t.block_threads > 256 || t.block_threads % 32 != 0)
+    return fail(ASH_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 256]");
+  if (t.blocks_per_sm < 1 || t.blocks_per_sm > 64) return fail(ASH_ERR_INVALID, "blocks_per_sm must be in [1, 64]");
+  if (t.max_probes < 0) return fail(ASH_ERR_INVALID, "max_probes must be >= 0");
+  if (!(t.max_used_fraction > 0.1f && t.max_used_fraction < 0.99f))
+    return fail(ASH_ERR_INVALID, "max_used_fraction must be in (0.1, 0.99)");
+  if (t.inline_value_bytes < 0) return fail(ASH_ERR_INVALID, "inline_value_bytes must be >= 0");
+  return ASH_OK;
+}
+
+int64_t slots_for(int64_t capacity, const ash_tuning& t) {
+  const int S = t.slots_per_bucket;
+  int64_t n = static_cast<int64_t>(std::ceil(static_cast<double>(capacity) * t.slots_per_capacity));
+  n = std::max<int64_t>(n, capacity + 1);
+  n = (n + S - 1) / S * S;
+  return n;
+}
+
+// Reads the control block (synchronises `st`).
+ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int* status) {
+  ASH_CUDA(cudaMemcpyAsync(m->ctrl_host, m->ctrl, sizeof(ash::Ctrl), cudaMemcpyDeviceToHost, st));
+  ASH_CUDA(cudaStreamSynchronize(st));
+  const unsigned long long tu = m->ctrl_host->top_used;
+  *top = static_cast<int64_t>(tu & 0xFFFFFFFFull);
+  *used = static_cast<int64_t>(tu >> 32);
+  if (status) *status = m->ctrl_host->status;
+  m->size_ub = *top;
+  m->used_ub = *used;
+  return ASH_OK;
+}
+
+ash_status status_from_bits(int bits) {
+  if (bits & ash::kStatusTableFull) return fail(ASH_ERR_TABLE_FULL, "a key found no free slot within max_probes buckets");
+  if (bits & ash::kStatusCapacity) return fail(ASH_ERR_CAPACITY, "the index heap ran out (capacity exceeded)");
+  return ASH_OK;
+}
+
+ash_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return ASH_OK;
+}
+
+// Allocates and initialises table, buffers and heap for `capacity`.
+ash_status alloc_storage(ash_map* m, int64_t capacity, cudaStream_t st) {
+  const int64_t n_slots = slots_for(capacity, m->tuning);
+  if (n_slots >= (int64_t{1} << 31)) return fail(ASH_ERR_INVALID, "capacity too large for 31-bit slot indices");
+  const ash::Launch L = launch_of(m, st);
+  m->slots = static_cast<uint64_t*>(dev_alloc(m, n_slots * 8, st));
+  m->kb = static_cast<int32_t*>(dev_alloc(m, capacity * m->ks * 4, st));
+  m->heap = static_cast<int32_t*>(dev_alloc(m, capacity * 4, st));
+  m->vb.assign(m->n_values, nullptr);
+  bool ok = m->slots && m->kb && m->heap;
+  for (int j = 0; j < m->n_values && ok; ++j) {
+    m->vb[j] = dev_alloc(m, capacity * m->row_bytes[j], st);
+    ok = m->vb[j] != nullptr;
+  }
+  if (!ok) return fail(ASH_ERR_OOM, "device allocation failed");
+  m->capacity = capacity;
+  m->n_slots = n_slots;
+  m->S = m->tuning.slots_per_bucket;
+  m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
+  ASH_CUDA(cudaMemsetAsync(m->slots, 0xFF, n_slots * 8, st));
+  ASH_CUDA(cudaMemsetAsync(m->kb, 0, capacity * m->ks * 4, st));
+  for (int j = 0; j < m->n_values; ++j) ASH_CUDA(cudaMemsetAsync(m->vb[j], 0, capacity * m->row_bytes[j], st));
+  ash::launch_iota(m->heap, 0, capacity, L);
+  return check_launch("alloc_storage");
+}
+
+void free_storage(ash_map* m, cudaStream_t st) {
+  dev_free(m, m->slots, st);
+  dev_free(m, m->kb, st);
+  dev_free(m, m->heap, st);
+  for (void* p : m->vb) dev_free(m, p, st);
+  m->slots = nullptr;
+  m->kb = nullptr;
+  m->heap = nullptr;
+  m->vb.assign(m->n_values, nullptr);
+}
+
+ash_status ensure_scratch(ash_map* m, int64_t bytes, cudaStream_t st) {
+  if (m->scratch_bytes >= bytes) return ASH_OK;
+  dev_free(m, m->scratch, st);
+  const int64_t want = std::max<int64_t>(bytes, m->scratch_bytes * 2);
+  m->scratch = static_cast<int32_t*>(dev_alloc(m, want, st));
+  if (!m->scratch) {
+    m->scratch_bytes = 0;
+    return fail(ASH_ERR_OOM, "scratch allocation failed");
+  }
+  m->scratch_bytes = want;
+  return ASH_OK;
+}
+
+// Rebuilds the table for new_capacity from the live entries (Sec. 4.5).
+// size: the exact live count (caller synchronised).
+ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream_t st) {
+  const ash::Launch L = launch_of(m, st);
+  // 1) collect the active indices
+  int32_t* list = static_cast<int32_t*>(dev_alloc(m, std::max<int64_t>(size, 1) * 4, st));
+  if (!list) return fail(ASH_ERR_OOM, "rehash list allocation failed");
+  ASH_CUDA(cudaMemsetAsync(&m->ctrl->count, 0, sizeof(unsigned long long), st));
+  ash::launch_list_active(m->slots, m->n_slots, m->ctrl, list, size, L);
+  ash_status s = check_launch("rehash listing");
+  if (s != ASH_OK) return s;
+
+  ash_map old = *m;  // shallow copy of the old storage pointers
+  const bool preserve = new_capacity >= m->capacity;
+  const int64_t n_slots = slots_for(new_capacity, m->tuning);
+  if (n_slots >= (int64_t{1} << 31)) {
+    dev_free(m, list, st);
+    return fail(ASH_ERR_INVALID, "capacity too large for 31-bit slot indices");
+  }
+  uint64_t* slots = static_cast<uint64_t*>(dev_alloc(m, n_slots * 8, st));
+  if (!slots) {
+    dev_free(m, list, st);
+    return fail(ASH_ERR_OOM, "rehash table allocation failed");
+  }
+  ASH_CUDA(cudaMemsetAsync(slots, 0xFF, n_slots * 8, st));
+
+  int32_t* kb = m->kb;
+  int32_t* heap = m->heap;
+  std::vector<void*> vb = m->vb;
+  const bool grow = new_capacity != m->capacity;
+  if (grow) {
+    kb = static_cast<int32_t*>(dev_alloc(m, new_capacity * m->ks * 4, st));
+    heap = static_cast<int32_t*>(dev_alloc(m, new_capacity * 4, st));
+    bool ok = kb && heap;
+    for (int j = 0; j < m->n_values && ok; ++j) {
+      vb[j] = dev_alloc(m, new_capacity * m->row_bytes[j], st);
+      ok = vb[j] != nullptr;
+    }
+    if (!ok) {
+      dev_free(m, list, st);
+      dev_free(m, slots, st);
+      return fail(ASH_ERR_OOM, "rehash buffer allocation failed");
+    }
+    if (preserve) {
+      // indices are kept: copy buffers, extend the heap with the new indices
+      ASH_CUDA(cudaMemcpyAsync(kb, m->kb, m->capacity * m->ks * 4, cudaMemcpyDeviceToDevice, st));
+      ASH_CUDA(cudaMemsetAsync(kb + m->capacity * m->ks, 0, (new_capacity - m->capacity) * m->ks * 4, st));
+      ASH_CUDA(cudaMemcpyAsync(heap, m->heap, m->capacity * 4, cudaMemcpyDeviceToDevice, st));
+      ash::launch_iota(heap, m->capacity, new_capacity, L);
+      for (int j = 0; j < m->n_values; ++j) {
+        const int64_t rb = m->row_bytes[j];
+        ASH_CUDA(cudaMemcpyAsync(vb[j], m->vb[j], m->capacity * rb, cudaMemcpyDeviceToDevice, st));
+        ASH_CUDA(cudaMemsetAsync(static_cast<char*>(vb[j]) + m->capacity * rb, 0, (new_capacity - m->capacity) * rb, st));
+      }
+    } else {
+      // compaction: entry j of the list becomes index j
+      ASH_CUDA(cudaMemsetAsync(kb, 0, new_capacity * m->ks * 4, st));
+      ash::launch_iota(heap, 0, new_capacity, L);
+      ash::ValueCopy vc{};
+      vc.n = m->n_values;
+      for (int j = 0; j < m->n_values; ++j) {
+        ASH_CUDA(cudaMemsetAsync(vb[j], 0, new_capacity * m->row_bytes[j], st));
+        vc.dst[j] = vb[j];
+        vc.src[j] = m->vb[j];
+        vc.row_bytes[j] = m->row_bytes[j];
+        vc.vec[j] = vec_width(m->row_bytes[j], vb[j], m->vb[j]);
+      }
+      ash::launch_gather_rows(vc, list, size, L);
+    }
+  }
+  // 2) re-insert the live keys into the new table
+  m->S = m->tuning.slots_per_bucket;
+  m->slots = slots;
+  m->n_slots = n_slots;
+  m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
+  m->capacity = new_capacity;
+  m->kb = kb;
+  m->heap = heap;
+  m->vb = vb;
+  ash::TableView tv = view_of(m);
+  m->K.rebuild(m->S, tv, old.kb, list, size, preserve ? 1 : 0, (!preserve) ? 1 : 0, L);
+  s = check_launch("rehash rebuild");
+  if (s != ASH_OK) return s;
+  ash::launch_set_top_used(m->ctrl, size, size, L);
+  // 3) release the old storage
+  dev_free(m, old.slots, st);
+  if (grow) {
+    dev_free(m, old.kb, st);
+    dev_free(m, old.heap, st);
+    for (void* p : old.vb) dev_free(m, p, st);
+  }
+  dev_free(m, list, st);
+  m->size_ub = size;
+  m->used_ub = size;
+  return check_launch("rehash");
+}
+
+// Makes room for a batch of n insert/activate keys: x2 growth when the live
+// count could pass the capacity (Sec. 4.5), and a table rebuild when used
+// slots (live + tombstones) could pass max_used_fraction.
+ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st) {
+  const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
+  const bool size_risk = m->size_ub + n > m->capacity;
+  const bool used_risk = m->used_ub + n > max_used;
+  if (!size_risk && !used_risk) return ASH_OK;
+  int64_t top, used;
+  ash_status s = refresh(m, st, &top, &used, nullptr);
+  if (s != ASH_OK) return s;
+  int64_t new_c = m->capacity;
+  if (top + n > m->capacity && m->tuning.auto_grow) {
+    new_c = std::max<int64_t>(m->capacity, 1);
+    while (top + n > new_c) new_c *= 2;
+  }
+  const int64_t max_used_new = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(slots_for(new_c, m->tuning)));
+  if (new_c != m->capacity || used + n > max_used_new) return rebuild_to(m, new_c, top, st);
+  return ASH_OK;
+}
+
+ash_status check_keys(const ash_map* m, const void* keys, int64_t n) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (n < 0 || n >= 0x7FFFFFFF) return fail(ASH_ERR_INVALID, "n must be in [0, 2^31 - 1)");
+  if (n > 0 && !keys) return fail(ASH_ERR_INVALID, "keys is NULL");
+  return ASH_OK;
+}
+
+ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* values_host, int64_t n, int32_t* idx,
+                       uint8_t* mask, cudaStream_t st) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (n == 0) return ASH_OK;
+  if (!idx || !mask) return fail(ASH_ERR_INVALID, "buf_indices and masks are required");
+  if (values_host && m->n_values > 0) {
+    for (int j = 0; j < m->n_values; ++j)
+      if (!values_host[j]) return fail(ASH_ERR_INVALID, "a value pointer is NULL");
+  }
+  DeviceGuard g(m->device);
+  m->last_stream = st;
+  s = ensure_room(m, n, st);
+  if (s != ASH_OK) return s;
+  const ash::Launch L = launch_of(m, st);
+  const ash::TableView tv = view_of(m);
+  m->K.claim(m->S, tv, keys, n, idx, L);
+  ash::ValueCopy vc{};
+  int64_t total_rb = 0;
+  if (values_host) {
+    vc.n = m->n_values;
+    for (int j = 0; j < m->n_values; ++j) {
+      vc.dst[j] = m->vb[j];
+      vc.src[j] = values_host[j];
+      vc.row_bytes[j] = m->row_bytes[j];
+      vc.vec[j] = vec_width(m->row_bytes[j], m->vb[j], values_host[j]);
+      total_rb += m->row_bytes[j];
+    }
+  }
+  const bool inline_values = vc.n > 0 && total_rb <= m->tuning.inline_value_bytes;
+  ash::ValueCopy none{};
+  m->K.commit(tv, keys, n, idx, mask, inline_values ? vc : none, L);
+  if (vc.n > 0 && !inline_values) ash::launch_scatter_rows(vc, idx, mask, n, L);
+  m->size_ub += n;
+  m->used_ub += n;
+  return check_launch("insert");
+}
+
+}  // namespace
+
+extern "C" {
+
+void ash_default_tuning(ash_tuning* out) {
+  if (!out) return;
+  out->slots_per_bucket = 4;
+  out->slots_per_capacity = 2.0f;
+  out->block_threads = 256;
+  out->blocks_per_sm = 8;
+  out->max_probes = 0;
+  out->auto_grow = 1;
+  out->max_used_fraction = 0.85f;
+  out->inline_value_bytes = 64;
+}
+
+ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return fail(ASH_ERR_INVALID, "alloc and free must both be set or both NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_alloc.alloc = alloc_fn;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return ASH_OK;
+}
+
+ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t* value_numel_host,
+                      const int32_t* value_dtypes_host, int device, const ash_tuning* tuning, ash_stream stream,
+                      ash_map** out_host) {
+  if (!out_host) return fail(ASH_ERR_INVALID, "out is NULL");
+  *out_host = nullptr;
+  if (key_dim < 1 || key_dim > 8) return fail(ASH_ERR_INVALID, "key_dim must be in 1..8");
+  if (capacity < 1) return fail(ASH_ERR_INVALID, "capacity must be >= 1");
+  if (n_values < 0 || n_values > ash::kMaxValues) return fail(ASH_ERR_INVALID, "n_values must be in 0..8");
+  if (n_values > 0 && (!value_numel_host || !value_dtypes_host)) return fail(ASH_ERR_INVALID, "value shapes/dtypes missing");
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return fail(ASH_ERR_INVALID, "no such CUDA device");
+  }
+  ash_map* m = new ash_map();
+  if (tuning) m->tuning = *tuning; else ash_default_tuning(&m->tuning);
+  ash_status s = validate_tuning(m->tuning);
+  if (s != ASH_OK) { delete m; return s; }
+  m->device = device;
+  m->key_dim = key_dim;
+  m->ks = key_dim <= 1 ? 1 : (key_dim <= 2 ? 2 : (key_dim <= 4 ? 4 : 8));
+  m->n_values = n_values;
+  for (int j = 0; j < n_values; ++j) {
+    const int64_t eb = dtype_bytes(value_dtypes_host[j]);
+    if (eb == 0 || value_numel_host[j] < 1) { delete m; return fail(ASH_ERR_INVALID, "bad value dtype or shape"); }
+    m->numel.push_back(value_numel_host[j]);
+    m->dtype.push_back(value_dtypes_host[j]);
+    m->row_bytes.push_back(eb * value_numel_host[j]);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    m->alloc = g_alloc;
+  }
+  m->K = kernels_for(key_dim);
+  DeviceGuard g(device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  if (cudaMallocHost(&m->ctrl_host, sizeof(ash::Ctrl)) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return fail(ASH_ERR_OOM, "pinned host allocation failed");
+  }
+  m->ctrl = static_cast<ash::Ctrl*>(dev_alloc(m, sizeof(ash::Ctrl), st));
+  if (!m->ctrl) { ash_destroy(m); return fail(ASH_ERR_OOM, "device allocation failed"); }
+  if (cudaMemsetAsync(m->ctrl, 0, sizeof(ash::Ctrl), st) != cudaSuccess) {
+    ash_destroy(m);
+    return cuda_fail(cudaGetLastError(), "ash_create");
+  }
+  s = alloc_storage(m, capacity, st);
+  if (s != ASH_OK) {
+    std::string msg = g_last_error;
+    ash_destroy(m);
+    return fail(s, msg);
+  }
+  *out_host = m;
+  return ASH_OK;
+}
+
+ash_status ash_destroy(ash_map* m) {
+  if (!m) return ASH_OK;
+  DeviceGuard g(m->device);
+  cudaStream_t st = m->last_stream;
+  free_storage(m, st);
+  dev_free(m, m->scratch, st);
+  dev_free(m, m->ctrl, st);
+  if (m->ctrl_host) cudaFreeHost(m->ctrl_host);
+  delete m;
+  return ASH_OK;
+}
+
+ash_status ash_insert(ash_map* m, const int32_t* keys, const void* const* values_host, int64_t n,
+                      int32_t* buf_indices, uint8_t* masks, ash_stream stream) {
+  if (m && m->n_values > 0 && n > 0 && !values_host) return fail(ASH_ERR_INVALID, "values are required for insert");
+  return insert_impl(m, keys, values_host, n, buf_indices, masks, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ash_status ash_activate(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_indices, uint8_t* masks,
+                        ash_stream stream) {
+  return insert_impl(m, keys, nullptr, n, buf_indices, masks, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_indices, uint8_t* masks,
+                    ash_stream stream) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (n == 0) return ASH_OK;
+  if (!buf_indices || !masks) return fail(ASH_ERR_INVALID, "buf_indices and masks are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  m->K.find(m->S, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
+  return check_launch("find");
+}
+
+ash_status ash_erase(ash_map* m, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (n == 0) return ASH_OK;
+  if (!masks) return fail(ASH_ERR_INVALID, "masks is required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  s = ensure_scratch(m, n * 4, st);
+  if (s != ASH_OK) return s;
+  const ash::Launch L = launch_of(m, st);
+  const ash::TableView tv = view_of(m);
+  m->K.erase_mark(m->S, tv, keys, n, m->scratch, L);
+  ash::launch_erase_resolve(m->S, tv, n, m->scratch, masks, L);
+  return check_launch("erase");
+}
+
+ash_status ash_get_active_indices(ash_map* m, int32_t* out, int64_t out_capacity, int64_t* count_host,
+                                  ash_stream stream) {
+  if (!m || !count_host) return fail(ASH_ERR_INVALID, "map and count_host are required");
+  if (out_capacity > 0 && !out) return fail(ASH_ERR_INVALID, "out is NULL");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  ASH_CUDA(cudaMemsetAsync(&m->ctrl->count, 0, sizeof(unsigned long long), st));
+  ash::launch_list_active(m->slots, m->n_slots, m->ctrl, out, std::max<int64_t>(out_capacity, 0), launch_of(m, st));
+  ash_status s = check_launch("get_active_indices");
+  if (s != ASH_OK) return s;
+  int64_t top, used;
+  s = refresh(m, st, &top, &used, nullptr);
+  if (s != ASH_OK) return s;
+  *count_host = static_cast<int64_t>(m->ctrl_host->count);
+  return ASH_OK;
+}
+
+ash_status ash_size(ash_map* m, int64_t* size_host, ash_stream stream) {
+  if (!m || !size_host) return fail(ASH_ERR_INVALID, "map and size_host are required");
+  DeviceGuard g(m->device);
+  int64_t top, used;
+  ash_status s = refresh(m, reinterpret_cast<cudaStream_t>(stream), &top, &used, nullptr);
+  if (s != ASH_OK) return s;
+  *size_host = top;
+  return ASH_OK;
+}
+
+int64_t ash_capacity(const ash_map* m) { return m ? m->capacity : 0; }
+int ash_key_dim(const ash_map* m) { return m ? m->key_dim : 0; }
+int ash_n_values(const ash_map* m) { return m ? m->n_values : 0; }
+
+ash_status ash_rehash(ash_map* m, int64_t new_capacity, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (new_capacity < 0) return fail(ASH_ERR_INVALID, "new_capacity must be >= 0");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  int64_t top, used;
+  ash_status s = refresh(m, st, &top, &used, nullptr);
+  if (s != ASH_OK) return s;
+  if (new_capacity == 0) new_capacity = 2 * m->capacity;
+  if (new_capacity < top) return fail(ASH_ERR_INVALID, "new_capacity is below the live count");
+  s = rebuild_to(m, new_capacity, top, st);
+  if (s != ASH_OK) return s;
+  ASH_CUDA(cudaStreamSynchronize(st));
+  return ASH_OK;
+}
+
+ash_status ash_reserve(ash_map* m, int64_t new_capacity, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (new_capacity <= m->capacity) return ASH_OK;
+  return ash_rehash(m, new_capacity, stream);
+}
+
+ash_status ash_clear(ash_map* m, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  const ash::Launch L = launch_of(m, st);
+  ASH_CUDA(cudaMemsetAsync(m->slots, 0xFF, m->n_slots * 8, st));
+  ash::launch_iota(m->heap, 0, m->capacity, L);
+  ash::launch_set_top_used(m->ctrl, 0, 0, L);
+  m->size_ub = 0;
+  m->used_ub = 0;
+  return check_launch("clear");
+}
+
+ash_status ash_key_buffer(ash_map* m, int32_t** ptr_host, int64_t* row_stride_host) {
+  if (!m || !ptr_host) return fail(ASH_ERR_INVALID, "map and ptr are required");
+  *ptr_host = m->kb;
+  if (row_stride_host) *row_stride_host = m->ks;
+  return ASH_OK;
+}
+
+ash_status ash_value_buffer(ash_map* m, int j, void** ptr_host, int64_t* row_bytes_host) {
+  if (!m || !ptr_host) return fail(ASH_ERR_INVALID, "map and ptr are required");
+  if (j < 0 || j >= m->n_values) return fail(ASH_ERR_INVALID, "value buffer index out of range");
+  *ptr_host = m->vb[j];
+  if (row_bytes_host) *row_bytes_host = m->row_bytes[j];
+  return ASH_OK;
+}
+
+ash_status ash_heap_buffer(ash_map* m, int32_t** heap_host, int32_t** top_host) {
+  if (!m || !heap_host) return fail(ASH_ERR_INVALID, "map and heap are required");
+  *heap_host = m->heap;
+  if (top_host) *top_host = reinterpret_cast<int32_t*>(&m->ctrl->top_used);  // low word (little endian)
+  return ASH_OK;
+}
+
+ash_status ash_gather_keys(ash_map* m, const int32_t* indices, int64_t n, int32_t* out, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (n < 0) return fail(ASH_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return ASH_OK;
+  if (!indices || !out) return fail(ASH_ERR_INVALID, "indices and out are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ash::launch_gather_keys(m->kb, m->ks, m->key_dim, m->capacity, indices, n, out, launch_of(m, st));
+  return check_launch("gather_keys");
+}
+
+ash_status ash_get_tuning(const ash_map* m, ash_tuning* out_host) {
+  if (!m || !out_host) return fail(ASH_ERR_INVALID, "map and out are required");
+  *out_host = m->tuning;
+  return ASH_OK;
+}
+
+ash_status ash_set_tuning(ash_map* m, const ash_tuning* t) {
+  if (!m || !t) return fail(ASH_ERR_INVALID, "map and tuning are required");
+  ash_status s = validate_tuning(*t);
+  if (s != ASH_OK) return s;
+  m->tuning = *t;  // S and slots_per_capacity apply at the next rebuild
+  m->tuning.slots_per_bucket = t->slots_per_bucket;
+  return ASH_OK;
+}
+
+ash_status ash_sync_status(ash_map* m, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int64_t top, used;
+  int bits = 0;
+  ash_status s = refresh(m, st, &top, &used, &bits);
+  if (s != ASH_OK) return s;
+  if (bits) {
+    ASH_CUDA(cudaMemsetAsync(&m->ctrl->status, 0, sizeof(int), st));
+    ASH_CUDA(cudaStreamSynchronize(st));
+  }
+  return status_from_bits(bits);
+}
+
+ash_status ash_quantize(const float* points, int64_t n_coords, float cell, int32_t* keys, ash_stream stream) {
+  if (n_coords < 0) return fail(ASH_ERR_INVALID, "n_coords must be >= 0");
+  if (n_coords == 0) return ASH_OK;
+  if (!points || !keys) return fail(ASH_ERR_INVALID, "points and keys are required");
+  if (!(cell > 0.0f) || !std::isfinite(cell)) return fail(ASH_ERR_INVALID, "cell must be finite and > 0");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  ash::Launch L;
+  L.stream = reinterpret_cast<cudaStream_t>(stream);
+  L.block = 256;
+  L.grid_cap = sm_count(dev) * 8;
+  ash::launch_quantize(points, n_coords, cell, keys, L);
+  return check_launch("quantize");
+}
+
+ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector_bytes, uint32_t seed,
+                                 uint32_t* sink, int64_t sink_len, ash_stream stream) {
+  if (!buf || !sink || sink_len < 1 || n_reads < 0) return fail(ASH_ERR_INVALID, "bad probe arguments");
+  if (sector_bytes != 32 && sector_bytes != 64) return fail(ASH_ERR_INVALID, "sector_bytes must be 32 or 64");
+  if (buf_bytes < 64 || buf_bytes % 64 != 0) return fail(ASH_ERR_INVALID, "buf_bytes must be a positive multiple of 64");
+  if ((reinterpret_cast<uintptr_t>(buf) & 63u) != 0) return fail(ASH_ERR_INVALID, "buf must be 64-byte aligned");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  ash::Launch L;
+  L.stream = reinterpret_cast<cudaStream_t>(stream);
+  L.block = 256;
+  L.grid_cap = sm_count(dev) * 8;
+  ash::launch_probe(buf, buf_bytes, n_reads, sector_bytes, seed, sink, sink_len, L);
+  return check_launch("probe");
+}
+
+const char* ash_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

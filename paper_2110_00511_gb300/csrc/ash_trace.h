@@ -1,0 +1,39 @@
+// Launch counting / event timing scope used by every kernel launcher.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ash {
+
+enum KernelKind {
+  kKFind = 0,
+  kKClaim,
+  kKCommit,
+  kKEraseMark,
+  kKEraseResolve,
+  kKRebuild,
+  kKListActive,
+  kKIota,
+  kKScatterRows,
+  kKGatherRows,
+  kKGatherKeys,
+  kKQuantize,
+  kKProbe,
+  kKSetCtrl,
+  kKernelKinds
+};
+
+class TraceScope {
+ public:
+  TraceScope(int kind, cudaStream_t stream);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  int kind_;
+  cudaStream_t stream_;
+  int rec_;
+};
+
+}  // namespace ash

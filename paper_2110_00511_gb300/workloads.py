@@ -54,7 +54,7 @@ def _distinct_keys(rng, u: int, key_dim: int, lo: int, hi: int) -> np.ndarray:
     """u distinct int32 keys drawn uniformly from [lo, hi)^key_dim."""
     span = hi - lo
     bits = max(1, math.ceil(math.log2(span)))
-    if bits * key_dim > 62:
+    if bits * key_dim > 63:
         raise ValueError("key range too wide for distinctness packing")
     got = np.empty((0, key_dim), np.int64)
     need = u

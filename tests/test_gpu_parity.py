@@ -1,0 +1,446 @@
+"""CUDA map vs the CPU oracle, element by element, through the C ABI.
+
+Bar: bit-exact for masks and stored keys, byte-exact for value rows, modulo
+the buffer-index permutation the paper leaves unspecified (see parity.py).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import assert_heap_permutation, assert_op_parity, assert_same_map, value_rows_for
+from paper_2110_00511_gb300 import ash, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2110_00511_gb300 import build
+    build.build()
+    ash.lib()
+    torch.cuda.init()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def tuning(**kw):
+    t = ash.default_tuning()
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def _rows(a, rb):
+    return np.ascontiguousarray(a).view(np.uint8).reshape(-1, rb)
+
+
+# ------------------------------------------------------------ plain map
+def test_plain_map_sequence():
+    """Insert 100k keys in [-64,64)^3 with float values, find half-hit
+    queries, erase 25%, re-find (the plain single-map workload)."""
+    case = workloads.plain_map_case(seed=0)
+    hm = ash.HashMap(3, case.capacity, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, case.capacity, [4])
+    k = dev(case.insert_keys)
+    gi, gm = hm.insert(k, [dev(case.insert_values)])
+    oi, omask = om.insert(case.insert_keys, [case.insert_values])
+    assert_op_parity(hm, case.insert_keys, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+    gi, gm = hm.find(dev(case.query_keys))
+    oi, omask = om.find(case.query_keys)
+    assert_op_parity(hm, case.query_keys, gi, gm, oi, omask, check_distinct=False)
+    hit = gm.cpu().numpy()
+    assert np.array_equal(value_rows_for(hm, 0, gi[gm]), om.value_buffer(0)[oi[hit]])
+    ge = hm.erase(dev(case.erase_keys))
+    oe = om.erase(case.erase_keys)
+    assert np.array_equal(ge.cpu().numpy(), oe)
+    gi, gm = hm.find(dev(case.query_keys))
+    oi, omask = om.find(case.query_keys)
+    assert_op_parity(hm, case.query_keys, gi, gm, oi, omask, check_distinct=False)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+# ------------------------------------------------------ dims x bucket sizes
+@pytest.mark.parametrize("d", range(1, 9))
+@pytest.mark.parametrize("S", [4, 8, 16])
+def test_dims_and_bucket_sizes(d, S):
+    rng = np.random.default_rng(100 * d + S)
+    n = 5003  # ragged: not a multiple of any block size
+    keys = rng.integers(-6, 6, size=(n, d)).astype(np.int32)
+    vals = rng.integers(-2**31, 2**31 - 1, size=n, dtype=np.int64).astype(np.int32)
+    hm = ash.HashMap(d, 4096, [(1,)], [torch.int32], tuning=tuning(slots_per_bucket=S))
+    om = oracle.OracleMap(d, 4096, [4])
+    gi, gm = hm.insert(dev(keys), [dev(vals)])
+    oi, omask = om.insert(keys, [vals])
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    gi, gm = hm.activate(dev(keys[::-1].copy()))
+    oi, omask = om.activate(keys[::-1].copy())
+    assert_op_parity(hm, keys[::-1].copy(), gi, gm, oi, omask)
+    er = keys[rng.integers(0, n, size=n // 2)]
+    assert np.array_equal(hm.erase(dev(er)).cpu().numpy(), om.erase(er))
+    q = rng.integers(-7, 7, size=(n, d)).astype(np.int32)
+    gi, gm = hm.find(dev(q))
+    oi, omask = om.find(q)
+    assert_op_parity(hm, q, gi, gm, oi, omask, check_distinct=False)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+# ------------------------------------------------------------ race stress
+def test_duplicate_race_stress():
+    """1M keys drawn from 1000 distinct triples (the heavy-duplicate setting
+    where Sec. 4.4.2 reports torn-copy races): exactly one winner per key, the
+    first occurrence, with its own value; repeated on fresh maps."""
+    rng = np.random.default_rng(5)
+    distinct = rng.integers(-2**30, 2**30, size=(1000, 3)).astype(np.int32)
+    for rep in range(5):
+        keys = distinct[rng.integers(0, 1000, size=1_000_000)]
+        vals = np.arange(1_000_000, dtype=np.int32)
+        hm = ash.HashMap(3, 1_000_000, [(1,)], [torch.int32])
+        gi, gm = hm.insert(dev(keys), [dev(vals)])
+        _, first = np.unique(keys, axis=0, return_index=True)
+        want = np.zeros(len(keys), bool)
+        want[first] = True
+        assert np.array_equal(gm.cpu().numpy(), want), f"winners are not the first occurrences (rep {rep})"
+        stored = hm.value_buffer(0)[gi[gm].long()].cpu().numpy().ravel()
+        assert np.array_equal(np.sort(stored), np.sort(first.astype(np.int32)))
+        kb = hm.key_buffer().cpu().numpy()
+        assert np.array_equal(kb[gi[gm].cpu().numpy()], keys[gm.cpu().numpy()])
+        assert hm.size() == 1000
+
+
+def test_erase_duplicates_first_occurrence():
+    rng = np.random.default_rng(6)
+    keys = rng.integers(-20, 20, size=(50_000, 3)).astype(np.int32)
+    hm = ash.HashMap(3, 100_000)
+    om = oracle.OracleMap(3, 100_000)
+    hm.activate(dev(keys))
+    om.activate(keys)
+    er = rng.integers(-25, 25, size=(80_000, 3)).astype(np.int32)
+    assert np.array_equal(hm.erase(dev(er)).cpu().numpy(), om.erase(er))
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+# --------------------------------------------------------- growth / rehash
+def test_auto_growth_matches_oracle():
+    rng = np.random.default_rng(7)
+    hm = ash.HashMap(3, 1000, [(2,)], [torch.float32])
+    om = oracle.OracleMap(3, 1000, [8])
+    for step in range(6):
+        n = int(rng.integers(500, 4000))
+        keys = rng.integers(-2**20, 2**20, size=(n, 3)).astype(np.int32)
+        vals = rng.random((n, 2), dtype=np.float32)
+        gi, gm = hm.insert(dev(keys), [dev(vals)])
+        oi, omask = om.insert(keys, [vals])
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+        assert hm.capacity() == om.capacity()
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+def test_rehash_preserves_indices_and_compacts():
+    rng = np.random.default_rng(8)
+    keys = rng.integers(-500, 500, size=(30_000, 3)).astype(np.int32)
+    vals = rng.random(30_000, dtype=np.float32)
+    hm = ash.HashMap(3, 40_000, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, 40_000, [4])
+    hm.insert(dev(keys), [dev(vals)])
+    om.insert(keys, [vals])
+    hm.erase(dev(keys[:5000]))
+    om.erase(keys[:5000])
+    q = dev(keys)
+    before_i, before_m = hm.find(q)
+    hm.rehash(100_000)
+    om.rehash(100_000)
+    after_i, after_m = hm.find(q)
+    assert torch.equal(before_m, after_m) and torch.equal(before_i, after_i), "growth must keep buffer indices"
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+    live = om.size()
+    hm.rehash(live)
+    om.rehash(live)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+    gi, gm = hm.find(q)
+    oi, omask = om.find(keys)
+    assert_op_parity(hm, keys, gi, gm, oi, omask, check_distinct=False)
+    # inserting after a compaction keeps working
+    more = rng.integers(600, 700, size=(1000, 3)).astype(np.int32)
+    mv = rng.random(1000, dtype=np.float32)
+    gi, gm = hm.insert(dev(more), [dev(mv)])
+    oi, omask = om.insert(more, [mv])
+    assert_op_parity(hm, more, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+
+
+def test_clear_and_reuse():
+    rng = np.random.default_rng(9)
+    keys = rng.integers(-50, 50, size=(20_000, 2)).astype(np.int32)
+    hm = ash.HashMap(2, 30_000)
+    om = oracle.OracleMap(2, 30_000)
+    for _ in range(3):
+        gi, gm = hm.activate(dev(keys))
+        oi, omask = om.activate(keys)
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+        hm.clear()
+        om.clear()
+        assert hm.size() == 0
+        assert_heap_permutation(hm)
+
+
+# ----------------------------------------------------------------- values
+def test_tsdf_block_values():
+    """Voxel-block values (Sec. 6.2 setup): tsdf float32[8,8,8] and weight
+    float16[8,8,8] rows, copied by the warp-per-row scatter kernel."""
+    rng = np.random.default_rng(10)
+    n = 20_000
+    keys = rng.integers(-40, 40, size=(n, 3)).astype(np.int32)
+    tsdf = rng.standard_normal((n, 8, 8, 8)).astype(np.float32)
+    w = rng.standard_normal((n, 8, 8, 8)).astype(np.float16)
+    hm = ash.HashMap(3, 1 << 15, [(8, 8, 8), (8, 8, 8)], [torch.float32, torch.float16])
+    om = oracle.OracleMap(3, 1 << 15, [2048, 1024])
+    gi, gm = hm.insert(dev(keys), [dev(tsdf), dev(w)])
+    oi, omask = om.insert(keys, [tsdf, w])
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+
+
+def test_value_dtypes_and_odd_row_sizes():
+    rng = np.random.default_rng(11)
+    n = 9_001
+    keys = rng.integers(-30, 30, size=(n, 4)).astype(np.int32)
+    v0 = rng.integers(0, 255, size=(n, 3)).astype(np.uint8)          # 3-byte rows
+    v1 = rng.standard_normal((n, 5)).astype(np.float16)              # 10-byte rows
+    v2 = rng.integers(-2**62, 2**62, size=(n, 1), dtype=np.int64)     # 8-byte rows
+    v3 = rng.standard_normal((n, 3)).astype(np.float64)              # 24-byte rows
+    hm = ash.HashMap(4, 1 << 14, [(3,), (5,), (1,), (3,)], [torch.uint8, torch.float16, torch.int64, torch.float64])
+    om = oracle.OracleMap(4, 1 << 14, [3, 10, 8, 24])
+    gi, gm = hm.insert(dev(keys), [dev(v0), dev(v1), dev(v2), dev(v3)])
+    oi, omask = om.insert(keys, [v0, v1, v2, v3])
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+
+
+def test_bfloat16_values():
+    rng = np.random.default_rng(12)
+    n = 4_000
+    keys = rng.integers(-20, 20, size=(n, 3)).astype(np.int32)
+    v = torch.randn(n, 4, dtype=torch.bfloat16, generator=torch.Generator().manual_seed(0))
+    hm = ash.HashMap(3, 1 << 13, [(4,)], [torch.bfloat16])
+    om = oracle.OracleMap(3, 1 << 13, [8])
+    gi, gm = hm.insert(dev(keys), [v.cuda()])
+    oi, omask = om.insert(keys, [v.view(torch.int16).numpy()])
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+
+
+# ------------------------------------------------------------ quantisation
+def test_quantize_bit_exact():
+    rng = np.random.default_rng(13)
+    pts = rng.normal(scale=5.0, size=(1_000_003, 3)).astype(np.float32)
+    pts[:5] = np.array([[0.5, -0.5, -0.0], [-1e-7, 9.999, 2.5], [-2.5, 0.0025, -0.0025],
+                        [1.0, -1.0, 0.1], [-0.1, 0.0049999, 0.005]], np.float32)
+    for cell in (0.005, 0.048, 0.05, 0.25, 1.0):
+        g = ash.ash_quantize(dev(pts), cell).cpu().numpy()
+        o = oracle.quantize(pts, cell)
+        assert np.array_equal(g, o), f"quantisation differs at cell {cell}"
+    # unaligned view takes the scalar path
+    flat = dev(pts).reshape(-1)[1:]
+    g = ash.ash_quantize(flat, 0.01).cpu().numpy()
+    assert np.array_equal(g, oracle.quantize(pts.reshape(-1)[1:], 0.01))
+
+
+# ----------------------------------------------------------- voxelization
+def test_voxelization_scene():
+    """Point-cloud voxelization (Sec. 6.1): 4M points, 5 mm voxels; insert
+    keys with point-index values, find every point's voxel, list the unique
+    voxels.  Compared with the oracle and with np.unique."""
+    pts = workloads.voxel_scene_points(n=4_000_000, seed=0)
+    n = pts.shape[0]
+    okeys = oracle.quantize(pts, 0.005)
+    gkeys = ash.ash_quantize(dev(pts), 0.005)
+    assert np.array_equal(gkeys.cpu().numpy(), okeys)
+    vals = np.arange(n, dtype=np.int32)
+    hm = ash.HashMap(3, n, [(1,)], [torch.int32])
+    om = oracle.OracleMap(3, n, [4])
+    gi, gm = hm.insert(gkeys.reshape(n, 3), [dev(vals)])
+    oi, omask = om.insert(okeys, [vals])
+    assert_op_parity(hm, okeys, gi, gm, oi, omask)
+    fi, fm = hm.find(gkeys.reshape(n, 3))
+    ofi, ofm = om.find(okeys)
+    assert_op_parity(hm, okeys, fi, fm, ofi, ofm, check_distinct=False)
+    assert_same_map(hm, om)
+    act = hm.active_indices()
+    uniq = hm.gather_keys(act).cpu().numpy()
+    want = np.unique(okeys, axis=0)
+    assert np.array_equal(uniq[np.lexsort(uniq.T[::-1])], want)
+
+
+@pytest.mark.parametrize("rho", [0.1, 0.5, 1.0])
+def test_uniqueness_sweep_1e6(rho):
+    keys = workloads.uniform_keys(1_000_000, rho, seed=3)
+    hm = ash.HashMap(3, len(keys))
+    om = oracle.OracleMap(3, len(keys))
+    gi, gm = hm.activate(dev(keys))
+    oi, omask = om.activate(keys)
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    fi, fm = hm.find(dev(keys))
+    ofi, ofm = om.find(keys)
+    assert_op_parity(hm, keys, fi, fm, ofi, ofm, check_distinct=False)
+    assert hm.size() == om.size()
+
+
+def test_uniqueness_sweep_1e7_properties():
+    """The full-size sweep point timed by the bench (10^7 keys): properties
+    that hold at any size, checked against np.unique rather than the oracle:
+    winners are exactly the first occurrences, and every position finds the
+    index its key's first occurrence received."""
+    keys = workloads.uniform_keys(10_000_000, 0.5, seed=4)
+    hm = ash.HashMap(3, len(keys))
+    gi, gm = hm.activate(dev(keys))
+    _, first, inverse = np.unique(keys, axis=0, return_index=True, return_inverse=True)
+    inverse = inverse.reshape(-1)
+    want = np.zeros(len(keys), bool)
+    want[first] = True
+    assert np.array_equal(gm.cpu().numpy(), want)
+    fi, fm = hm.find(dev(keys))
+    assert bool(fm.all())
+    gi_np = gi.cpu().numpy()
+    assert np.array_equal(fi.cpu().numpy(), gi_np[first[inverse]])
+    kb = hm.key_buffer()
+    assert torch.equal(kb[fi.long()], dev(keys))
+    assert hm.size() == len(first)
+    assert_heap_permutation(hm)
+
+
+# --------------------------------------------------------------- TSDF frames
+def test_tsdf_frames_and_neighbourhood():
+    """Voxel-block activation over synthetic depth frames (Sec. 6.2, reduced
+    to 6 frames at 1/4 resolution), then the 27-neighbourhood find of every
+    active block (the radius search of Sec. 6.2)."""
+    hm = ash.HashMap(3, 1 << 16)
+    om = oracle.OracleMap(3, 1 << 16)
+    for keys in workloads.tsdf_block_frames(n_frames=6, seed=1, stride=4):
+        gi, gm = hm.activate(dev(keys))
+        oi, omask = om.activate(keys)
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+    act = hm.active_indices()
+    blocks = hm.gather_keys(act).cpu().numpy()
+    offs = workloads.radius_offsets(1)
+    q = (blocks[:, None, :] + offs[None, :, :]).reshape(-1, 3).astype(np.int32)
+    gi, gm = hm.find(dev(q))
+    oi, omask = om.find(q)
+    assert_op_parity(hm, q, gi, gm, oi, omask, check_distinct=False)
+    assert gm.reshape(-1, 27)[:, 13].all(), "every block must find itself"
+
+
+# ------------------------------------------------------------------ edges
+def test_edge_cases():
+    hm = ash.HashMap(3, 64, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, 64, [4])
+    empty = torch.empty((0, 3), dtype=torch.int32, device="cuda")
+    gi, gm = hm.insert(empty, [torch.empty(0, device="cuda")])
+    assert gi.numel() == 0 and hm.size() == 0
+    gi, gm = hm.find(empty)
+    assert gm.numel() == 0
+    assert hm.erase(empty).numel() == 0
+    gi, gm = hm.find(dev(np.zeros((5, 3), np.int32)))
+    assert not gm.any() and (gi == -1).all()
+    assert not hm.erase(dev(np.zeros((5, 3), np.int32))).any()
+    ext = np.array([[-2**31, 2**31 - 1, 0], [2**31 - 1, -2**31, -1], [0, 0, 0], [-1, -1, -1],
+                    [-2**31, -2**31, -2**31], [2**31 - 1] * 3, [0, 0, 0]], np.int32)
+    v = np.arange(len(ext), dtype=np.float32)
+    gi, gm = hm.insert(dev(ext), [dev(v)])
+    oi, omask = om.insert(ext, [v])
+    assert_op_parity(hm, ext, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+    for n in (1, 31, 33, 255, 257, 1025):
+        rng = np.random.default_rng(n)
+        k = rng.integers(-3, 3, size=(n, 3)).astype(np.int32)
+        vv = rng.random(n, dtype=np.float32)
+        gi, gm = hm.insert(dev(k), [dev(vv)])
+        oi, omask = om.insert(k, [vv])
+        assert_op_parity(hm, k, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+def test_capacity_error_without_growth():
+    t = tuning(auto_grow=0)
+    hm = ash.HashMap(3, 100, tuning=t)
+    keys = dev(np.arange(600, dtype=np.int32).reshape(200, 3))
+    gi, gm = hm.activate(keys)
+    with pytest.raises(ash.AshError) as e:
+        hm.sync_status()
+    assert e.value.status == ash.ASH_ERR_CAPACITY
+    assert int(gm.sum()) == 100 and hm.size() == 100
+    assert (gi[~gm] == -1).all()
+    assert_heap_permutation(hm)
+    hm.sync_status()  # status was cleared
+
+
+def test_table_full_reported_not_trapped():
+    t = tuning(max_probes=1, slots_per_bucket=4, slots_per_capacity=1.05, auto_grow=0)
+    hm = ash.HashMap(2, 4096, tuning=t)
+    keys = dev(np.random.default_rng(1).integers(-2**20, 2**20, size=(4096, 2)).astype(np.int32))
+    gi, gm = hm.activate(keys)
+    with pytest.raises(ash.AshError) as e:
+        hm.sync_status()
+    assert e.value.status == ash.ASH_ERR_TABLE_FULL
+    fi, fm = hm.find(keys)
+    assert torch.equal(fm, gm), "keys that failed must not be findable; inserted ones must be"
+    assert_heap_permutation(hm)
+
+
+def test_churn_with_tombstones():
+    """Insert/erase cycles on a small table: tombstones accumulate and the
+    used-slot bound triggers table rebuilds; results stay identical."""
+    rng = np.random.default_rng(14)
+    hm = ash.HashMap(3, 1024, [(1,)], [torch.int32], tuning=tuning(slots_per_bucket=4))
+    om = oracle.OracleMap(3, 1024, [4])
+    for r in range(40):
+        k = rng.integers(-15, 15, size=(700, 3)).astype(np.int32)
+        v = rng.integers(0, 1000, size=700).astype(np.int32)
+        gi, gm = hm.insert(dev(k), [dev(v)])
+        oi, omask = om.insert(k, [v])
+        assert_op_parity(hm, k, gi, gm, oi, omask)
+        e = rng.integers(-15, 15, size=(900, 3)).astype(np.int32)
+        assert np.array_equal(hm.erase(dev(e)).cpu().numpy(), om.erase(e))
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+def test_side_stream_and_gather():
+    rng = np.random.default_rng(15)
+    keys = rng.integers(-100, 100, size=(50_000, 3)).astype(np.int32)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        hm = ash.HashMap(3, 60_000)
+        gi, gm = hm.activate(dev(keys))
+        g = hm.gather_keys(gi[gm])
+    s.synchronize()
+    assert np.array_equal(g.cpu().numpy(), keys[gm.cpu().numpy()])
+    neg = hm.gather_keys(torch.tensor([-1, -5], dtype=torch.int32, device="cuda"))
+    assert (neg == 0).all()
+
+
+def test_torch_allocator_hook():
+    ash.use_torch_allocator(True)
+    try:
+        rng = np.random.default_rng(16)
+        keys = rng.integers(-100, 100, size=(30_000, 3)).astype(np.int32)
+        hm = ash.HashMap(3, 1000)
+        om = oracle.OracleMap(3, 1000)
+        gi, gm = hm.activate(dev(keys))
+        oi, omask = om.activate(keys)
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+        assert_same_map(hm, om)
+        del hm
+    finally:
+        ash.use_torch_allocator(False)
