@@ -135,6 +135,24 @@ ash_status ash_find(ash_map* map, const int32_t* keys, int64_t n, int32_t* buf_i
  * Uses n * 4 bytes of library-owned scratch (grown on demand). */
 ash_status ash_erase(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
 
+/* Allocation-free erase.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library allocate device memory (a host
+ * whose device memory is fully budgeted by its own allocator, or a
+ * latency-bound loop where a first-time allocation, which may synchronise the
+ * device, is not acceptable).  Same semantics and outputs as ash_erase, but
+ * its per-key scratch is a fixed device array inside libash.so
+ * (ASH_ERASE_NOALLOC_MAX_KEYS int32 = 4 MiB, held on every GPU that loads the
+ * library until the process exits) instead of map-owned memory; it calls no
+ * allocator.
+ *   n > ASH_ERASE_NOALLOC_MAX_KEYS: returns ASH_ERR_INVALID, nothing runs.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array, which keeps the previous call's contents:
+ *   calls whose kernels can overlap on the GPU (other streams, other maps on
+ *   the same device) race on it and must be ordered by the caller. */
+#define ASH_ERASE_NOALLOC_MAX_KEYS (1 << 20)
+ash_status ash_erase_noalloc(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
+
 /* Lists the buffer indices of all live entries (the "active" entries that
  * Sec. 4.5 collects for rehash).  Order unspecified.  Writes at most
  * out_capacity indices to out and the live count to *count_host.

@@ -59,6 +59,7 @@ _SIGS = {
     "ash_activate": (_I32, [_P, _P, _I64, _P, _P, _P]),
     "ash_find": (_I32, [_P, _P, _I64, _P, _P, _P]),
     "ash_erase": (_I32, [_P, _P, _I64, _P, _P]),
+    "ash_erase_noalloc": (_I32, [_P, _P, _I64, _P, _P]),
     "ash_get_active_indices": (_I32, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "ash_size": (_I32, [_P, ctypes.POINTER(_I64), _P]),
     "ash_capacity": (_I64, [_P]),
@@ -218,6 +219,20 @@ def ash_find(handle, keys, buf_indices, masks, stream=None):
 def ash_erase(handle, keys, masks, stream=None):
     _check(lib().ash_erase(handle, _ptr(keys), keys.shape[0], _ptr(masks),
                            stream if stream is not None else _stream(keys.device)))
+
+
+# Largest n accepted by ash_erase_noalloc (ASH_ERASE_NOALLOC_MAX_KEYS in ash.h).
+ASH_ERASE_NOALLOC_MAX_KEYS = 1 << 20
+
+
+def ash_erase_noalloc(handle, keys, masks, stream=None):
+    """Erase without any device allocation by the library: for callers that
+    cannot let a library allocate (fully budgeted device memory, or loops
+    where a first-time allocation may synchronise the device).  Uses a fixed
+    4 MiB device array shared by all calls; n <= ASH_ERASE_NOALLOC_MAX_KEYS;
+    calls that can overlap on the GPU must be ordered by the caller."""
+    _check(lib().ash_erase_noalloc(handle, _ptr(keys), keys.shape[0], _ptr(masks),
+                                   stream if stream is not None else _stream(keys.device)))
 
 
 def ash_get_active_indices(handle, out, stream=None):

@@ -754,3 +754,67 @@ ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_r
 const char* ash_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free erase
+//
+// Some callers cannot let a library allocate device memory: a host whose
+// device memory is fully budgeted by its own allocator, or a latency-bound
+// loop where a first-time cudaMalloc (which can synchronise the device) is
+// not acceptable.  ash_erase may grow map-owned scratch; this variant
+// instead uses the fixed array below, so it allocates nothing.
+//
+// The array lives in device global memory for the life of the process on
+// every GPU that loads this library (ASH_ERASE_NOALLOC_MAX_KEYS int32 =
+// 4 MiB).  Host code must not use the symbol's name as a pointer (it is a
+// host-side stand-in); the device address is obtained once per device with
+// cudaGetSymbolAddress, with that device current, on the first call that
+// runs on it.  All calls share the array: two calls whose kernels overlap
+// on the GPU (different streams, or different maps on the same device)
+// race on it and must be ordered by the caller.  Nothing in it needs to
+// start at zero: the mark kernel writes every entry that the resolve kernel
+// reads.
+namespace {
+
+static __device__ __align__(256) int32_t g_erase_noalloc_scratch[ASH_ERASE_NOALLOC_MAX_KEYS];
+
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_ptr[64] = {};
+
+ash_status noalloc_scratch(int device, int32_t** out) {
+  if (device < 0 || device >= 64) return fail(ASH_ERR_INVALID, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_erase_noalloc_scratch);  // device is current here
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return fail(ASH_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[device] = static_cast<int32_t*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return ASH_OK;
+}
+
+}  // namespace
+
+extern "C" ash_status ash_erase_noalloc(ash_map* m, const int32_t* keys, int64_t n, uint8_t* masks,
+                                        ash_stream stream) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (n > ASH_ERASE_NOALLOC_MAX_KEYS)
+    return fail(ASH_ERR_INVALID, "ash_erase_noalloc: n exceeds ASH_ERASE_NOALLOC_MAX_KEYS (1048576)");
+  if (n == 0) return ASH_OK;
+  if (!masks) return fail(ASH_ERR_INVALID, "masks is required");
+  DeviceGuard g(m->device);
+  int32_t* scratch = nullptr;
+  s = noalloc_scratch(m->device, &scratch);
+  if (s != ASH_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  const ash::Launch L = launch_of(m, st);
+  const ash::TableView tv = view_of(m);
+  m->K.erase_mark(m->S, tv, keys, n, scratch, L);
+  ash::launch_erase_resolve(m->S, tv, n, scratch, masks, L);
+  return check_launch("erase_noalloc");
+}
