@@ -172,8 +172,10 @@ def bytes_commit(n, n_slotted, n_win, value_bytes, d=3):
     return n * 9 + n_slotted * 32 + n_win * (4 + 4 * d + 4 * key_stride(d) + 32 + 2 * value_bytes)
 
 
-def bytes_list(n_slots, n_live):
-    return n_slots * 8 + n_live * 4
+def bytes_list(capacity, n_live):
+    """Heap tail read (4 per free index), free bitmap cleared, marked and read
+    (c/8 bytes each), live indices written (4 each)."""
+    return 4 * (capacity - n_live) + 3 * ((capacity + 7) // 8) + 4 * n_live
 
 
 def bytes_quantize(n_coords):
@@ -181,7 +183,9 @@ def bytes_quantize(n_coords):
 
 
 def bytes_gather_keys(n, d=3):
-    return n * (4 + 32 + 4 * d)
+    """Index in (4), kB row read (4*stride; the listing is made of ascending
+    runs, so rows are read nearly sequentially), key out (4d)."""
+    return n * (4 + 4 * key_stride(d) + 4 * d)
 
 
 def bytes_erase(n_present, n_absent, d=3):
@@ -358,18 +362,12 @@ def main(argv=None):
 
     # ---------------------------------------------------------- roofline
     hbm_peak, peak_kind = peaks()
-    n_slots = 0
-    hm_probe = ash.HashMap(3, N, [(1,)], [torch.int32], device=device)
-    t = hm_probe.tuning()
-    del hm_probe
-    import math
-    n_slots = int(math.ceil(N * t.slots_per_capacity / t.slots_per_bucket)) * t.slots_per_bucket
     per_launch_bytes = {
         "quantize": bytes_quantize(3 * N),
         "insert_claim": bytes_claim(N),
         "insert_commit": bytes_commit(N, N, n_unique, 4),
         "find": bytes_find(N, 0),
-        "list_active": bytes_list(n_slots, n_unique),
+        "list_active": bytes_list(N, n_unique),
         "gather_keys": bytes_gather_keys(n_unique),
         "heap_iota": 4 * N,
     }
@@ -545,7 +543,7 @@ def per_op_figures(args, device, hbm_peak):
     rec("activate", min(ms_act), bytes_claim(n) + bytes_commit(n, n, n_unique, 0), n)
     import math
     n_slots = int(math.ceil(n * t.slots_per_capacity / t.slots_per_bucket)) * t.slots_per_bucket
-    rec("list_active", timed(lambda: hm.active_indices()), bytes_list(n_slots, n_unique), n_unique)
+    rec("list_active", timed(lambda: hm.active_indices()), bytes_list(n, n_unique), n_unique)
     ms_er = []
     for _ in range(2):
         h3 = ash.HashMap(3, n, device=device)
@@ -563,7 +561,7 @@ def per_op_figures(args, device, hbm_peak):
     ms_rh = timed(lambda: hm.rehash(2 * hm.capacity()), reps=1)
     c = hm.capacity() // 2
     n_slots2 = 2 * n_slots
-    rh_bytes = bytes_list(n_slots, n_unique) + 8 * n_slots2 + n_unique * (4 + 16 + 64) + 2 * c * (16 + 4 + 4)
+    rh_bytes = bytes_list(c, n_unique) + 8 * n_slots2 + n_unique * (4 + 16 + 64) + 2 * c * (16 + 4 + 4)
     rec("rehash_x2", ms_rh, rh_bytes, n_unique)
     del hm
     return out

@@ -72,8 +72,12 @@ typedef struct ash_tuning {
   int32_t max_probes;         /* bucket probes before a key fails; 0 = every bucket */
   int32_t auto_grow;          /* 1: insert/activate double the capacity until size+n <= c (Sec. 4.5) */
   float max_used_fraction;    /* rebuild the table when live+erased slots would pass this fraction */
-  int32_t inline_value_bytes; /* value rows up to this many bytes (all buffers) are copied by the
-                                 committing thread; larger rows by a warp-per-row scatter kernel */
+  int32_t inline_value_bytes; /* a map with ONE value buffer whose rows are 4, 8 or 16 bytes (at most
+                                 this limit, both bases aligned to the row size) has them copied by
+                                 the committing thread; other layouts use a warp-per-row scatter
+                                 kernel after the commit */
+  int32_t keys_per_thread;    /* 1, 2 or 4 keys handled together by each thread of the find, claim
+                                 and commit kernels (more independent memory requests in flight) */
 } ash_tuning;
 
 /* Fills *out with the defaults. */
@@ -97,8 +101,10 @@ ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* c
  *   value_numel_host:  elements per value row of buffer j (e.g. 512 for 8^3).
  *   value_dtypes_host: ash_dtype per buffer.
  *   tuning:            NULL for the defaults.
- * The key buffer is int32 [c, key_stride] (key_stride = 1, 2, 4 or 8 >= key_dim,
- * padding zeroed), value buffer j is [c, numel_j] of its dtype, zero-filled.
+ * The key buffer is int32 [c, key_stride] (key_stride = 1, 2, 4 or 8 >= key_dim;
+ * a row is written whole, padding zeroed, when its index is handed out; rows
+ * never handed out are unspecified), value buffer j is [c, numel_j] of its
+ * dtype, zero-filled.
  * The table starts empty and the heap as the identity with t = 0. */
 ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t* value_numel_host,
                       const int32_t* value_dtypes_host, int device, const ash_tuning* tuning,
@@ -154,8 +160,10 @@ ash_status ash_erase(ash_map* map, const int32_t* keys, int64_t n, uint8_t* mask
 ash_status ash_erase_noalloc(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
 
 /* Lists the buffer indices of all live entries (the "active" entries that
- * Sec. 4.5 collects for rehash).  Order unspecified.  Writes at most
- * out_capacity indices to out and the live count to *count_host.
+ * Sec. 4.5 collects for rehash).  The order is unspecified; it is made of
+ * ascending runs (each covering 8192 consecutive indices).  Writes at most
+ * out_capacity indices to out and the live count to *count_host.  Uses
+ * about c/8 bytes of library-owned scratch (grown on demand).
  * Synchronises the stream. */
 ash_status ash_get_active_indices(ash_map* map, int32_t* out, int64_t out_capacity,
                                   int64_t* count_host, ash_stream stream);

@@ -21,69 +21,66 @@ void launch_erase_resolve(int S, const TableView& t, int64_t n, const int32_t* s
 }
 
 // ----------------------------------------------------------- active listing
-// Block-wide exclusive scan of a small per-thread count.
-__device__ __forceinline__ int block_exclusive_scan(int v, int& total, int* s_warp) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int n_warps = blockDim.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= o) x += y;
+// Live indices are the complement of the heap's free part h[t..c) (the heap
+// keeps active + free a permutation of 0..c-1).  Free indices are marked in a
+// bitmap; one kernel then compacts the unmarked bits: each block owns 8192
+// consecutive indices (one bitmap word per thread), ranks its live ones with a
+// block scan and reserves its output range with one atomic.  Each block's output is an ascending run, so
+// gathers over the list read the key and value buffers in long sequential
+// runs.  No table scan is needed.
+constexpr int kListThreads = 256;
+constexpr int kListWordsPerBlock = kListThreads;  // one bitmap word (32 indices) per thread
+
+__global__ void mark_free_kernel(const int32_t* __restrict__ heap, int64_t capacity, const Ctrl* __restrict__ ctrl,
+                                 uint32_t* __restrict__ words) {
+  const int64_t t = static_cast<int64_t>(static_cast<uint32_t>(ctrl->top_used));
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t j = t + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < capacity; j += stride) {
+    const uint32_t i = static_cast<uint32_t>(heap[j]);
+    atomicOr(words + (i >> 5), 1u << (i & 31));
   }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int w = 0; w < n_warps; ++w) {
-      const int c = s_warp[w];
-      s_warp[w] = acc;
-      acc += c;
-    }
-    s_warp[n_warps] = acc;
-  }
-  __syncthreads();
-  total = s_warp[n_warps];
-  return s_warp[warp] + x - v;
 }
 
-// Each thread reads one 32-byte group of 4 slots; committed slots (low word
-// below kClaimBit) contribute their buffer index.  One atomic per block
-// reserves the output range.
-__global__ void __launch_bounds__(256) list_active_kernel(const uint64_t* __restrict__ slots, int64_t n_groups,
-                                                          Ctrl* ctrl, int32_t* __restrict__ out, int64_t out_cap) {
+__global__ void __launch_bounds__(kListThreads) compact_live_kernel(const uint32_t* __restrict__ words,
+                                                                    int64_t capacity, Ctrl* ctrl,
+                                                                    int32_t* __restrict__ out, int64_t out_cap) {
   __shared__ int s_warp[33];
   __shared__ unsigned long long s_base;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n_groups; base += stride) {
-    const int64_t g = base + threadIdx.x;
-    uint64_t w[4] = {kEmpty, kEmpty, kEmpty, kEmpty};
-    if (g < n_groups) load32<true>(slots + 4 * g, w[0], w[1], w[2], w[3]);
-    int c = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) c += (lo32(w[q]) < kClaimBit) ? 1 : 0;
-    int total;
-    const int off = block_exclusive_scan(c, total, s_warp);
-    if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctrl->count, static_cast<unsigned long long>(total)) : 0ull;
-    __syncthreads();
-    int64_t o = static_cast<int64_t>(s_base) + off;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (lo32(w[q]) < kClaimBit) {
-        if (o < out_cap) out[o] = static_cast<int32_t>(lo32(w[q]));
-        ++o;
-      }
-    }
-    __syncthreads();
+  const int64_t wi = static_cast<int64_t>(blockIdx.x) * kListThreads + threadIdx.x;
+  uint32_t live = ~words[wi];
+  const int64_t lo = wi * 32;
+  if (lo >= capacity) live = 0;
+  else if (lo + 32 > capacity) live &= (1u << (capacity - lo)) - 1u;
+  int total;
+  const int off = block_exclusive_scan(__popc(live), total, s_warp);
+  if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctrl->count, static_cast<unsigned long long>(total)) : 0ull;
+  __syncthreads();
+  int64_t o = static_cast<int64_t>(s_base) + off;
+  while (live) {
+    const int b = __ffs(live) - 1;
+    live &= live - 1u;
+    if (o < out_cap) out[o] = static_cast<int32_t>(lo + b);
+    ++o;
   }
 }
 
-void launch_list_active(const uint64_t* slots, int64_t n_slots, Ctrl* ctrl, int32_t* out, int64_t out_cap,
-                        const Launch& L) {
-  const int64_t groups = n_slots / 4;
-  TraceScope ts(kKListActive, L.stream);
-  list_active_kernel<<<grid_for(groups, L), L.block, 0, L.stream>>>(slots, groups, ctrl, out, out_cap);
+int64_t list_scratch_words(int64_t capacity) {
+  const int64_t words = (capacity + 31) / 32;
+  return (words + kListWordsPerBlock - 1) / kListWordsPerBlock * kListWordsPerBlock;
+}
+
+int64_t list_scratch_bytes(int64_t capacity) { return list_scratch_words(capacity) * 4; }
+
+void launch_list_active(const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch, int32_t* out,
+                        int64_t out_cap, const Launch& L) {
+  const int64_t words = list_scratch_words(capacity);
+  const int n_blocks = static_cast<int>(words / kListWordsPerBlock);
+  uint32_t* bitmap = static_cast<uint32_t*>(scratch);
+  TraceScope ts(kKListActive, L.stream, 2);
+  cudaMemsetAsync(bitmap, 0, words * 4, L.stream);
+  cudaMemsetAsync(&ctrl->count, 0, sizeof(unsigned long long), L.stream);
+  mark_free_kernel<<<grid_for(capacity, L), L.block, 0, L.stream>>>(heap, capacity, ctrl, bitmap);
+  compact_live_kernel<<<n_blocks, kListThreads, 0, L.stream>>>(bitmap, capacity, ctrl, out, out_cap);
 }
 
 // ------------------------------------------------------------------- heap
@@ -158,14 +155,23 @@ void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, con
 }
 
 // --------------------------------------------------------------- key gather
+// Thread per output row: out[r, 0:d] = kB(indices[r]) (zeros for indices
+// outside [0, capacity)).
 __global__ void gather_keys_kernel(const int32_t* __restrict__ kb, int ks, int d, int64_t capacity,
                                    const int32_t* __restrict__ indices, int64_t n, int32_t* __restrict__ out) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n * d; e += stride) {
-    const int64_t r = e / d;
-    const int c = static_cast<int>(e - r * d);
-    const int32_t i = indices[r];
-    out[e] = (i >= 0 && i < capacity) ? kb[static_cast<int64_t>(i) * ks + c] : 0;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const int32_t i = __ldg(indices + r);
+    const bool ok = i >= 0 && i < capacity;
+    const int32_t* src = kb + static_cast<int64_t>(ok ? i : 0) * ks;
+    int32_t* dst = out + r * d;
+    if (ks == 4) {
+      const int4 v = ok ? __ldg(reinterpret_cast<const int4*>(src)) : make_int4(0, 0, 0, 0);
+      const int32_t a[4] = {v.x, v.y, v.z, v.w};
+      for (int c = 0; c < d; ++c) dst[c] = a[c];
+    } else {
+      for (int c = 0; c < d; ++c) dst[c] = ok ? __ldg(src + c) : 0;
+    }
   }
 }
 
@@ -173,7 +179,7 @@ void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, cons
                         int32_t* out, const Launch& L) {
   if (n == 0) return;
   TraceScope ts(kKGatherKeys, L.stream);
-  gather_keys_kernel<<<grid_for(n * d, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, out);
+  gather_keys_kernel<<<grid_for(n, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, out);
 }
 
 // ------------------------------------------------------------- quantisation

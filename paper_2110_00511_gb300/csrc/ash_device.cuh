@@ -251,6 +251,35 @@ __device__ __forceinline__ void block_rank(bool flag, int& rank, int& total, int
   total = s_warp[n_warps];
 }
 
+// Block-wide exclusive scan of a small per-thread count; returns this
+// thread's offset and sets the block total.  Every thread of the block must
+// call it (it contains __syncthreads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int& total, int* s_warp) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int n_warps = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < n_warps; ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = acc;
+      acc += c;
+    }
+    s_warp[n_warps] = acc;
+  }
+  __syncthreads();
+  total = s_warp[n_warps];
+  return s_warp[warp] + x - v;
+}
+
 __device__ __forceinline__ int block_count(bool flag, int* s_cnt) {
   const unsigned ballot = __ballot_sync(0xFFFFFFFFu, flag);
   if (threadIdx.x == 0) *s_cnt = 0;

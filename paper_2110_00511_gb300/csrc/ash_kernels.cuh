@@ -1,7 +1,9 @@
 // Hash map kernels, templated on the key dimension D and the bucket size S.
 //
-// find            one thread per query key: hash, probe buckets from the home
-//                 bucket, verify fingerprint matches against kB (Eq. (4)).
+// find            KPT query keys per thread: hash, load the home buckets of all
+//                 KPT keys back to back, verify the fingerprint match of each
+//                 against kB (Eq. (4)); keys that overflow their home bucket
+//                 take the scalar probe loop.
 // insert/activate two kernels (Sec. 4.3.1 lazy insertion, redesigned):
 //   claim         one thread per input key.  A key already committed is
 //                 rejected.  Otherwise the thread claims the first EMPTY slot
@@ -35,33 +37,99 @@
 namespace ash {
 
 // ---------------------------------------------------------------------- find
+// Scalar lookup of input row pos from its home bucket (the slow path of find).
 template <int D, int S>
+__device__ __noinline__ int32_t find_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
+  int32_t k[D];
+  load_input_key<D>(keys, pos, k);
+  const uint64_t h = hash_key<D>(k);
+  const uint32_t fp = fingerprint(h);
+  uint32_t b = home_bucket(h, t.n_buckets);
+  for (uint32_t probe = 0; probe < t.max_probes; ++probe) {
+    uint64_t w[S];
+    load_bucket<S, true>(t.slots + static_cast<size_t>(b) * S, w);
+    bool stop = false;
+    int32_t out = -1;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      stop |= (w[s] == kEmpty);
+      if (out < 0 && hi32(w[s]) == fp && lo32(w[s]) < kClaimBit && kb_equal<D>(t.kb, lo32(w[s]), k))
+        out = static_cast<int32_t>(lo32(w[s]));
+    }
+    if (out >= 0) return out;
+    if (stop) return -1;
+    b = next_bucket(b, t.n_buckets);
+  }
+  return -1;
+}
+
+// KPT keys per thread: positions base, base + blockDim.x, ... so every load
+// instruction stays coalesced across the warp.  All home buckets are loaded
+// before any is examined, and all verify loads are issued before any compare.
+template <int D, int S, int KPT>
 __global__ void __launch_bounds__(256) find_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
                                                    int32_t* __restrict__ idx, uint8_t* __restrict__ mask) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; pos < n; pos += stride) {
-    int32_t k[D];
-    load_input_key<D>(keys, pos, k);
-    const uint64_t h = hash_key<D>(k);
-    const uint32_t fp = fingerprint(h);
-    uint32_t b = home_bucket(h, t.n_buckets);
-    int32_t out = -1;
-    for (uint32_t probe = 0; probe < t.max_probes; ++probe) {
-      uint64_t w[S];
-      load_bucket<S, true>(t.slots + static_cast<size_t>(b) * S, w);
-      bool stop = false;
+  constexpr int KS = KeyStride<D>::value;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT + threadIdx.x; base < n; base += step) {
+    int32_t k[KPT][D];
+    uint32_t fp[KPT], b[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (pos < n) {
+        load_input_key<D>(keys, pos, k[q]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) k[q][j] = 0;
+      }
+      const uint64_t h = hash_key<D>(k[q]);
+      fp[q] = fingerprint(h);
+      b[q] = home_bucket(h, t.n_buckets);
+    }
+    uint64_t w[KPT][S];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) load_bucket<S, true>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
+    uint32_t cand[KPT];
+    int ncand[KPT];
+    bool stop[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      cand[q] = kNoIndex;
+      ncand[q] = 0;
+      stop[q] = false;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        stop |= (w[s] == kEmpty);
-        if (out < 0 && hi32(w[s]) == fp && lo32(w[s]) < kClaimBit) {
-          if (kb_equal<D>(t.kb, lo32(w[s]), k)) out = static_cast<int32_t>(lo32(w[s]));
-        }
+        stop[q] |= (w[q][s] == kEmpty);
+        const bool m = hi32(w[q][s]) == fp[q] && lo32(w[q][s]) < kClaimBit;
+        if (m && ncand[q] == 0) cand[q] = lo32(w[q][s]);
+        ncand[q] += m ? 1 : 0;
       }
-      if (out >= 0 || stop) break;
-      b = next_bucket(b, t.n_buckets);
     }
-    idx[pos] = out;
-    mask[pos] = out >= 0 ? 1 : 0;
+    int32_t row[KPT][KS];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      if (ncand[q] > 0) {
+        load_kb<D>(t.kb, cand[q], row[q]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < KS; ++j) row[q][j] = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (pos < n) {
+        bool eq = ncand[q] > 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
+        int32_t out = -1;
+        if (eq) out = static_cast<int32_t>(cand[q]);
+        else if (ncand[q] > 0 || !stop[q]) out = find_one<D, S>(t, keys, pos);  // rare
+        idx[pos] = out;
+        mask[pos] = out >= 0 ? 1 : 0;
+      }
+    }
   }
 }
 
@@ -80,8 +148,14 @@ __device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_
   return kb_equal<D>(kb, lo, k) ? 2 : 0;
 }
 
+// The full claim protocol for one key, from its home bucket (the slow path of
+// the claim kernel; safe to run after a fast-path attempt that changed
+// nothing).  1) any slot of the bucket holding an equal key ends the search;
+// 2) otherwise the EMPTY slots are claimed in order, and a lost CAS re-checks
+// the winner's word for an equal key; 3) a bucket without EMPTY slots sends
+// the key to the next bucket.
 template <int D, int S>
-__device__ __forceinline__ int32_t claim_one(const TableView& t, const int32_t* __restrict__ keys, int64_t pos) {
+__device__ __noinline__ int32_t claim_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
   const uint64_t h = hash_key<D>(k);
@@ -92,7 +166,6 @@ __device__ __forceinline__ int32_t claim_one(const TableView& t, const int32_t* 
     uint64_t* bp = t.slots + static_cast<size_t>(b) * S;
     uint64_t w[S];
     load_bucket<S, false>(bp, w);
-    // 1) an equal key already in the bucket (claimed or committed)
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int m = claim_match<D>(w[s], fp, k, keys, t.kb);
@@ -103,8 +176,6 @@ __device__ __forceinline__ int32_t claim_one(const TableView& t, const int32_t* 
         return static_cast<int32_t>(b * S + s);
       }
     }
-    // 2) claim the EMPTY slots of the bucket in order; a lost CAS re-checks
-    //    the winner's word for an equal key
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if (w[s] == kEmpty) {
@@ -127,35 +198,180 @@ __device__ __forceinline__ int32_t claim_one(const TableView& t, const int32_t* 
   return kClaimFailed;
 }
 
-template <int D, int S>
+// KPT keys per thread.  Fast path per key, on its home bucket only: if the
+// bucket holds exactly one slot with the key's fingerprint, compare once
+// (claimant's input row or kB row); on no match, CAS the first EMPTY slot.
+// The loads, compares and CASes of the KPT keys are issued back to back.
+// Anything else (several fingerprint matches, a lost CAS, a full bucket)
+// runs claim_one, which is safe because the fast path changed nothing then.
+template <int D, int S, int KPT>
 __global__ void __launch_bounds__(256) claim_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
                                                     int32_t* __restrict__ slot_out) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; pos < n; pos += stride)
-    slot_out[pos] = claim_one<D, S>(t, keys, pos);
+  constexpr int KS = KeyStride<D>::value;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT + threadIdx.x; base < n; base += step) {
+    int32_t k[KPT][D];
+    uint32_t fp[KPT], b[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (pos < n) {
+        load_input_key<D>(keys, pos, k[q]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) k[q][j] = 0;
+      }
+      const uint64_t h = hash_key<D>(k[q]);
+      fp[q] = fingerprint(h);
+      b[q] = home_bucket(h, t.n_buckets);
+    }
+    uint64_t w[KPT][S];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) load_bucket<S, false>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
+    int cs[KPT], nc[KPT], es[KPT];
+    uint32_t clo[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      cs[q] = -1;
+      nc[q] = 0;
+      es[q] = -1;
+      clo[q] = kNoIndex;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const bool m = lo32(w[q][s]) != kNoIndex && hi32(w[q][s]) == fp[q];
+        if (m && nc[q] == 0) {
+          cs[q] = s;
+          clo[q] = lo32(w[q][s]);
+        }
+        nc[q] += m ? 1 : 0;
+        if (es[q] < 0 && w[q][s] == kEmpty) es[q] = s;
+      }
+    }
+    int32_t row[KPT][KS];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      if (nc[q] > 0) {
+        if (clo[q] & kClaimBit) {
+          int32_t o[D];
+          load_input_key<D>(keys, clo[q] & ~kClaimBit, o);
+#pragma unroll
+          for (int j = 0; j < KS; ++j) row[q][j] = j < D ? o[j] : 0;
+        } else {
+          load_kb<D>(t.kb, clo[q], row[q]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KS; ++j) row[q][j] = 0;
+      }
+    }
+    int32_t res[KPT];
+    bool cas[KPT], slow[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      res[q] = kClaimFailed;
+      cas[q] = false;
+      slow[q] = false;
+      if (pos < n) {
+        bool eq = nc[q] > 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
+        if (eq) {
+          if (clo[q] & kClaimBit) {
+            if ((clo[q] & ~kClaimBit) > static_cast<uint32_t>(pos)) {
+              const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
+              atomicMin(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + cs[q]),
+                        static_cast<unsigned long long>(mine));
+            }
+            res[q] = static_cast<int32_t>(b[q] * S + cs[q]);
+          } else {
+            res[q] = kClaimExists;
+          }
+        } else if (nc[q] > 1 || es[q] < 0) {
+          slow[q] = true;
+        } else {
+          cas[q] = true;
+        }
+      }
+    }
+    uint64_t old[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      old[q] = 0;
+      if (cas[q]) {
+        const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+        const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
+        old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + es[q]),
+                           static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (cas[q]) {
+        if (old[q] == kEmpty) res[q] = static_cast<int32_t>(b[q] * S + es[q]);
+        else slow[q] = true;
+      }
+      if (slow[q]) res[q] = claim_one<D, S>(t, keys, pos);  // rare
+      if (pos < n) slot_out[pos] = res[q];
+    }
+  }
 }
 
 // ------------------------------------------------------------ insert: commit
-template <int D>
-__global__ void __launch_bounds__(256, 4) commit_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+// One value buffer whose rows are exactly 4, 8 or 16 bytes with both bases
+// aligned to the row size: the committing thread copies its row as one
+// vector.  Other layouts use the scatter kernel after the commit.
+struct ValueRow {
+  void* dst;
+  const void* src;
+  int64_t row_bytes;  // 4, 8 or 16
+  int vec;
+  int pad;
+};
+
+__device__ __forceinline__ void copy_small_row(const ValueRow& v, int32_t i, int64_t pos) {
+  char* d = static_cast<char*>(v.dst) + static_cast<int64_t>(i) * v.row_bytes;
+  const char* s = static_cast<const char*>(v.src) + pos * v.row_bytes;
+  if (v.row_bytes == 16) *reinterpret_cast<uint4*>(d) = __ldg(reinterpret_cast<const uint4*>(s));
+  else if (v.row_bytes == 8) *reinterpret_cast<uint2*>(d) = __ldg(reinterpret_cast<const uint2*>(s));
+  else *reinterpret_cast<uint32_t*>(d) = __ldg(reinterpret_cast<const uint32_t*>(s));
+}
+
+// KPT keys per thread per block iteration (blockDim.x * KPT keys): the slot
+// index and slot word of every key are loaded first (independent loads), one
+// block-wide scan ranks the winners and ONE heap atomic serves the iteration
+// (Sec. 4.3: t is raised by the number of indices taken).  Winners then write
+// kB(i), the value row, the committed slot word and their outputs.
+template <int D, int KPT, bool VAL>
+__global__ void __launch_bounds__(256) commit_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
                                                      int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
-                                                     ValueCopy vc) {
+                                                     ValueRow v) {
   __shared__ int s_warp[33];
   __shared__ int s_base;
   __shared__ int s_got;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
-    const int64_t pos = base + threadIdx.x;
-    const bool active = pos < n;
-    const int32_t s = active ? idx[pos] : -1;
-    uint64_t w = 0;
-    bool win = false;
-    if (s >= 0) {
-      w = load_slot_relaxed(t.slots + s);
-      win = (lo32(w) == (kClaimBit | static_cast<uint32_t>(pos)));
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
+  for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step) {
+    const int64_t base = base0 + threadIdx.x;
+    int32_t s[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      s[q] = pos < n ? idx[pos] : -1;
     }
-    int rank, total;
-    block_rank(win, rank, total, s_warp);
+    uint64_t w[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) w[q] = s[q] >= 0 ? load_slot_relaxed(t.slots + s[q]) : 0ull;
+    bool win[KPT];
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      win[q] = s[q] >= 0 && lo32(w[q]) == (kClaimBit | static_cast<uint32_t>(pos));
+      cnt += win[q] ? 1 : 0;
+    }
+    int total;
+    const int off = block_exclusive_scan(cnt, total, s_warp);
     if (threadIdx.x == 0) {
       int got = 0, top = 0;
       if (total > 0) {
@@ -174,29 +390,32 @@ __global__ void __launch_bounds__(256, 4) commit_kernel(TableView t, const int32
       s_got = got;
     }
     __syncthreads();
-    if (win) {
-      if (rank < s_got) {
-        const int32_t i = t.heap[s_base + rank];
-        int32_t k[D];
-        load_input_key<D>(keys, pos, k);
-        store_kb<D>(t.kb, static_cast<uint32_t>(i), k);
+    int r = off;
 #pragma unroll
-        for (int j = 0; j < kMaxValues; ++j) {
-          if (j < vc.n)
-            copy_row(static_cast<char*>(vc.dst[j]) + static_cast<int64_t>(i) * vc.row_bytes[j],
-                     static_cast<const char*>(vc.src[j]) + pos * vc.row_bytes[j], vc.row_bytes[j], vc.vec[j], 0, 1);
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (pos < n) {
+        if (win[q]) {
+          if (r < s_got) {
+            const int32_t i = t.heap[s_base + r];
+            int32_t k[D];
+            load_input_key<D>(keys, pos, k);
+            store_kb<D>(t.kb, static_cast<uint32_t>(i), k);
+            if constexpr (VAL) copy_small_row(v, i, pos);
+            t.slots[s[q]] = (static_cast<uint64_t>(hi32(w[q])) << 32) | static_cast<uint32_t>(i);
+            idx[pos] = i;
+            mask[pos] = 1;
+          } else {
+            t.slots[s[q]] = kTombstone;
+            idx[pos] = -1;
+            mask[pos] = 0;
+          }
+          ++r;
+        } else {
+          idx[pos] = -1;
+          mask[pos] = 0;
         }
-        t.slots[s] = (static_cast<uint64_t>(hi32(w)) << 32) | static_cast<uint32_t>(i);
-        idx[pos] = i;
-        mask[pos] = 1;
-      } else {
-        t.slots[s] = kTombstone;
-        idx[pos] = -1;
-        mask[pos] = 0;
       }
-    } else if (active) {
-      idx[pos] = -1;
-      mask[pos] = 0;
     }
     __syncthreads();
   }
@@ -339,41 +558,72 @@ inline int grid_for(int64_t n, const Launch& L) {
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
-// Function table for one key dimension (filled in by ash_dim<D>.cu).
+// Function table for one key dimension (filled in by ash_dim.cu).  S: slots
+// per bucket (4, 8, 16); kpt: keys per thread (1, 2, 4).
 struct DimKernels {
-  void (*find)(int S, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
-  void (*claim)(int S, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
-  void (*commit)(const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const ValueCopy&, const Launch&);
+  void (*find)(int S, int kpt, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
+  void (*claim)(int S, int kpt, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
+  void (*commit)(int kpt, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const ValueRow*,
+                 const Launch&);
   void (*erase_mark)(int S, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
   void (*rebuild)(int S, const TableView&, const int32_t*, const int32_t*, int64_t, int, int, const Launch&);
 };
 
 template <int D>
 struct DimLaunchers {
-  template <int S>
-  static void find_s(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
+  template <int S, int KPT>
+  static void find_sk(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
     TraceScope ts(kKFind, L.stream);
-    find_kernel<D, S><<<grid_for(n, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask);
-  }
-  static void find(int S, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
-    if (S == 4) find_s<4>(t, keys, n, idx, mask, L);
-    else if (S == 8) find_s<8>(t, keys, n, idx, mask, L);
-    else find_s<16>(t, keys, n, idx, mask, L);
+    find_kernel<D, S, KPT><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask);
   }
   template <int S>
-  static void claim_s(const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
+  static void find_s(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                     const Launch& L) {
+    if (kpt >= 4) find_sk<S, 4>(t, keys, n, idx, mask, L);
+    else if (kpt == 2) find_sk<S, 2>(t, keys, n, idx, mask, L);
+    else find_sk<S, 1>(t, keys, n, idx, mask, L);
+  }
+  static void find(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                   const Launch& L) {
+    if (S == 4) find_s<4>(kpt, t, keys, n, idx, mask, L);
+    else if (S == 8) find_s<8>(kpt, t, keys, n, idx, mask, L);
+    else find_s<16>(kpt, t, keys, n, idx, mask, L);
+  }
+  template <int S, int KPT>
+  static void claim_sk(const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
     TraceScope ts(kKClaim, L.stream);
-    claim_kernel<D, S><<<grid_for(n, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    claim_kernel<D, S, KPT><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
   }
-  static void claim(int S, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
-    if (S == 4) claim_s<4>(t, keys, n, slot_out, L);
-    else if (S == 8) claim_s<8>(t, keys, n, slot_out, L);
-    else claim_s<16>(t, keys, n, slot_out, L);
+  template <int S>
+  static void claim_s(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
+    if (kpt >= 4) claim_sk<S, 4>(t, keys, n, slot_out, L);
+    else if (kpt == 2) claim_sk<S, 2>(t, keys, n, slot_out, L);
+    else claim_sk<S, 1>(t, keys, n, slot_out, L);
   }
-  static void commit(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
-                     const ValueCopy& vc, const Launch& L) {
+  static void claim(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out,
+                    const Launch& L) {
+    if (S == 4) claim_s<4>(kpt, t, keys, n, slot_out, L);
+    else if (S == 8) claim_s<8>(kpt, t, keys, n, slot_out, L);
+    else claim_s<16>(kpt, t, keys, n, slot_out, L);
+  }
+  template <int KPT, bool VAL>
+  static void commit_kv(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                        const ValueRow& v, const Launch& L) {
     TraceScope ts(kKCommit, L.stream);
-    commit_kernel<D><<<grid_for(n, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask, vc);
+    commit_kernel<D, KPT, VAL><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
+  }
+  template <bool VAL>
+  static void commit_v(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                       const ValueRow& v, const Launch& L) {
+    if (kpt >= 4) commit_kv<4, VAL>(t, keys, n, idx, mask, v, L);
+    else if (kpt == 2) commit_kv<2, VAL>(t, keys, n, idx, mask, v, L);
+    else commit_kv<1, VAL>(t, keys, n, idx, mask, v, L);
+  }
+  // v == nullptr: no inline value copy.
+  static void commit(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                     const ValueRow* v, const Launch& L) {
+    if (v) commit_v<true>(kpt, t, keys, n, idx, mask, *v, L);
+    else commit_v<false>(kpt, t, keys, n, idx, mask, ValueRow{}, L);
   }
   template <int S>
   static void erase_mark_s(const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
@@ -408,7 +658,7 @@ struct DimLaunchers {
   }
 };
 
-// Defined in ash_dim<D>.cu.
+// Defined in ash_dim.cu (one translation unit per key dimension).
 DimKernels dim_kernels_1();
 DimKernels dim_kernels_2();
 DimKernels dim_kernels_3();

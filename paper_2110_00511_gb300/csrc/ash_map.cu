@@ -49,6 +49,34 @@ std::mutex g_mu;
 Allocator g_alloc;
 bool g_pool_ready[64] = {};
 
+// Pinned host mirrors of the maps' control blocks come from pinned pages
+// allocated once and recycled, so creating and destroying maps does not pay
+// for cudaMallocHost / cudaFreeHost each time.
+std::mutex g_pin_mu;
+std::vector<ash::Ctrl*> g_pin_free;
+
+ash::Ctrl* pinned_ctrl_take() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr int kPerPage = 128;
+    void* page = nullptr;
+    if (cudaMallocHost(&page, sizeof(ash::Ctrl) * kPerPage) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = kPerPage - 1; i >= 0; --i) g_pin_free.push_back(static_cast<ash::Ctrl*>(page) + i);
+  }
+  ash::Ctrl* c = g_pin_free.back();
+  g_pin_free.pop_back();
+  return c;
+}
+
+void pinned_ctrl_give(ash::Ctrl* c) {
+  if (!c) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(c);
+}
+
 int64_t dtype_bytes(int32_t dt) {
   switch (dt) {
     case ASH_F32: case ASH_I32: return 4;
@@ -112,8 +140,10 @@ struct ash_map {
   std::vector<void*> vb;
   ash::Ctrl* ctrl = nullptr;
   ash::Ctrl* ctrl_host = nullptr;  // pinned mirror for synchronising reads
-  int32_t* scratch = nullptr;
+  int32_t* scratch = nullptr;      // erase: one slot index per key
   int64_t scratch_bytes = 0;
+  void* list_scratch = nullptr;    // listing: free-index bitmap + block counts
+  int64_t list_scratch_bytes = 0;
   int64_t size_ub = 0;  // upper bound of live entries since the last sync
   int64_t used_ub = 0;  // upper bound of used slots since the last sync
   ash_tuning tuning{};
@@ -203,6 +233,8 @@ ash_status validate_tuning(const ash_tuning& t) {
   if (!(t.max_used_fraction > 0.1f && t.max_used_fraction < 0.99f))
     return fail(ASH_ERR_INVALID, "max_used_fraction must be in (0.1, 0.99)");
   if (t.inline_value_bytes < 0) return fail(ASH_ERR_INVALID, "inline_value_bytes must be >= 0");
+  if (t.keys_per_thread != 1 && t.keys_per_thread != 2 && t.keys_per_thread != 4)
+    return fail(ASH_ERR_INVALID, "keys_per_thread must be 1, 2 or 4");
   return ASH_OK;
 }
 
@@ -259,7 +291,6 @@ ash_status alloc_storage(ash_map* m, int64_t capacity, cudaStream_t st) {
   m->S = m->tuning.slots_per_bucket;
   m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
   ASH_CUDA(cudaMemsetAsync(m->slots, 0xFF, n_slots * 8, st));
-  ASH_CUDA(cudaMemsetAsync(m->kb, 0, capacity * m->ks * 4, st));
   for (int j = 0; j < m->n_values; ++j) ASH_CUDA(cudaMemsetAsync(m->vb[j], 0, capacity * m->row_bytes[j], st));
   ash::launch_iota(m->heap, 0, capacity, L);
   return check_launch("alloc_storage");
@@ -289,6 +320,19 @@ ash_status ensure_scratch(ash_map* m, int64_t bytes, cudaStream_t st) {
   return ASH_OK;
 }
 
+ash_status ensure_list_scratch(ash_map* m, cudaStream_t st) {
+  const int64_t need = ash::list_scratch_bytes(m->capacity);
+  if (m->list_scratch_bytes >= need) return ASH_OK;
+  dev_free(m, m->list_scratch, st);
+  m->list_scratch = dev_alloc(m, need, st);
+  if (!m->list_scratch) {
+    m->list_scratch_bytes = 0;
+    return fail(ASH_ERR_OOM, "listing scratch allocation failed");
+  }
+  m->list_scratch_bytes = need;
+  return ASH_OK;
+}
+
 // Rebuilds the table for new_capacity from the live entries (Sec. 4.5).
 // size: the exact live count (caller synchronised).
 ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream_t st) {
@@ -296,9 +340,13 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
   // 1) collect the active indices
   int32_t* list = static_cast<int32_t*>(dev_alloc(m, std::max<int64_t>(size, 1) * 4, st));
   if (!list) return fail(ASH_ERR_OOM, "rehash list allocation failed");
-  ASH_CUDA(cudaMemsetAsync(&m->ctrl->count, 0, sizeof(unsigned long long), st));
-  ash::launch_list_active(m->slots, m->n_slots, m->ctrl, list, size, L);
-  ash_status s = check_launch("rehash listing");
+  ash_status s = ensure_list_scratch(m, st);
+  if (s != ASH_OK) {
+    dev_free(m, list, st);
+    return s;
+  }
+  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, list, size, L);
+  s = check_launch("rehash listing");
   if (s != ASH_OK) return s;
 
   ash_map old = *m;  // shallow copy of the old storage pointers
@@ -335,7 +383,6 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
     if (preserve) {
       // indices are kept: copy buffers, extend the heap with the new indices
       ASH_CUDA(cudaMemcpyAsync(kb, m->kb, m->capacity * m->ks * 4, cudaMemcpyDeviceToDevice, st));
-      ASH_CUDA(cudaMemsetAsync(kb + m->capacity * m->ks, 0, (new_capacity - m->capacity) * m->ks * 4, st));
       ASH_CUDA(cudaMemcpyAsync(heap, m->heap, m->capacity * 4, cudaMemcpyDeviceToDevice, st));
       ash::launch_iota(heap, m->capacity, new_capacity, L);
       for (int j = 0; j < m->n_values; ++j) {
@@ -345,7 +392,6 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
       }
     } else {
       // compaction: entry j of the list becomes index j
-      ASH_CUDA(cudaMemsetAsync(kb, 0, new_capacity * m->ks * 4, st));
       ash::launch_iota(heap, 0, new_capacity, L);
       ash::ValueCopy vc{};
       vc.n = m->n_values;
@@ -430,23 +476,34 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   if (s != ASH_OK) return s;
   const ash::Launch L = launch_of(m, st);
   const ash::TableView tv = view_of(m);
-  m->K.claim(m->S, tv, keys, n, idx, L);
+  const int kpt = m->tuning.keys_per_thread;
+  m->K.claim(m->S, kpt, tv, keys, n, idx, L);
+  // one value buffer with small rows: copied by the committing thread;
+  // anything else: warp-per-row scatter after the commit
+  bool inline_value = false;
+  ash::ValueRow vr{};
   ash::ValueCopy vc{};
-  int64_t total_rb = 0;
-  if (values_host) {
-    vc.n = m->n_values;
-    for (int j = 0; j < m->n_values; ++j) {
-      vc.dst[j] = m->vb[j];
-      vc.src[j] = values_host[j];
-      vc.row_bytes[j] = m->row_bytes[j];
-      vc.vec[j] = vec_width(m->row_bytes[j], m->vb[j], values_host[j]);
-      total_rb += m->row_bytes[j];
+  if (values_host && m->n_values > 0) {
+    const int64_t rb0 = m->row_bytes[0];
+    if (m->n_values == 1 && rb0 <= m->tuning.inline_value_bytes && (rb0 == 4 || rb0 == 8 || rb0 == 16) &&
+        vec_width(rb0, m->vb[0], values_host[0]) == rb0) {
+      inline_value = true;
+      vr.dst = m->vb[0];
+      vr.src = values_host[0];
+      vr.row_bytes = m->row_bytes[0];
+      vr.vec = vec_width(m->row_bytes[0], m->vb[0], values_host[0]);
+    } else {
+      vc.n = m->n_values;
+      for (int j = 0; j < m->n_values; ++j) {
+        vc.dst[j] = m->vb[j];
+        vc.src[j] = values_host[j];
+        vc.row_bytes[j] = m->row_bytes[j];
+        vc.vec[j] = vec_width(m->row_bytes[j], m->vb[j], values_host[j]);
+      }
     }
   }
-  const bool inline_values = vc.n > 0 && total_rb <= m->tuning.inline_value_bytes;
-  ash::ValueCopy none{};
-  m->K.commit(tv, keys, n, idx, mask, inline_values ? vc : none, L);
-  if (vc.n > 0 && !inline_values) ash::launch_scatter_rows(vc, idx, mask, n, L);
+  m->K.commit(kpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+  if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
   m->size_ub += n;
   m->used_ub += n;
   return check_launch("insert");
@@ -465,7 +522,8 @@ void ash_default_tuning(ash_tuning* out) {
   out->max_probes = 0;
   out->auto_grow = 1;
   out->max_used_fraction = 0.85f;
-  out->inline_value_bytes = 64;
+  out->inline_value_bytes = 16;
+  out->keys_per_thread = 2;
 }
 
 ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {
@@ -514,8 +572,8 @@ ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t
   DeviceGuard g(device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
-  if (cudaMallocHost(&m->ctrl_host, sizeof(ash::Ctrl)) != cudaSuccess) {
-    cudaGetLastError();
+  m->ctrl_host = pinned_ctrl_take();
+  if (!m->ctrl_host) {
     delete m;
     return fail(ASH_ERR_OOM, "pinned host allocation failed");
   }
@@ -541,8 +599,9 @@ ash_status ash_destroy(ash_map* m) {
   cudaStream_t st = m->last_stream;
   free_storage(m, st);
   dev_free(m, m->scratch, st);
+  dev_free(m, m->list_scratch, st);
   dev_free(m, m->ctrl, st);
-  if (m->ctrl_host) cudaFreeHost(m->ctrl_host);
+  pinned_ctrl_give(m->ctrl_host);
   delete m;
   return ASH_OK;
 }
@@ -567,7 +626,7 @@ ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_ind
   DeviceGuard g(m->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
-  m->K.find(m->S, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
+  m->K.find(m->S, m->tuning.keys_per_thread, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
   return check_launch("find");
 }
 
@@ -595,9 +654,11 @@ ash_status ash_get_active_indices(ash_map* m, int32_t* out, int64_t out_capacity
   DeviceGuard g(m->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
-  ASH_CUDA(cudaMemsetAsync(&m->ctrl->count, 0, sizeof(unsigned long long), st));
-  ash::launch_list_active(m->slots, m->n_slots, m->ctrl, out, std::max<int64_t>(out_capacity, 0), launch_of(m, st));
-  ash_status s = check_launch("get_active_indices");
+  ash_status s = ensure_list_scratch(m, st);
+  if (s != ASH_OK) return s;
+  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
+                          launch_of(m, st));
+  s = check_launch("get_active_indices");
   if (s != ASH_OK) return s;
   int64_t top, used;
   s = refresh(m, st, &top, &used, nullptr);

@@ -50,9 +50,10 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
-TraceScope::TraceScope(int kind, cudaStream_t stream) : kind_(kind), stream_(stream), rec_(-1) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (kind >= 0 && kind < kKernelKinds) g_launches_by[kind].fetch_add(1, std::memory_order_relaxed);
+TraceScope::TraceScope(int kind, cudaStream_t stream, int launches) : kind_(kind), stream_(stream), rec_(-1) {
+  g_launches.fetch_add(static_cast<unsigned long long>(launches), std::memory_order_relaxed);
+  if (kind >= 0 && kind < kKernelKinds)
+    g_launches_by[kind].fetch_add(static_cast<unsigned long long>(launches), std::memory_order_relaxed);
   if (g_on.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_mu);
     Rec r{kind, take_event(), take_event()};

@@ -25,7 +25,8 @@ enum KernelKind {
 
 class TraceScope {
  public:
-  TraceScope(int kind, cudaStream_t stream);
+  // `launches`: kernels launched inside the scope (counted, timed together).
+  TraceScope(int kind, cudaStream_t stream, int launches = 1);
   ~TraceScope();
   TraceScope(const TraceScope&) = delete;
   TraceScope& operator=(const TraceScope&) = delete;
