@@ -211,6 +211,45 @@ ash_status ash_set_tuning(ash_map* map, const ash_tuning* tuning_host);
  * kernel of this map reported since the last check. */
 ash_status ash_sync_status(ash_map* map, ash_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched execution: one CUDA-graph launch services many maps (the paper has
+ * no batched form; it applies the per-map operations above to many maps at
+ * once).  Phases run in the order insert/activate -> find -> erase, each as
+ * one persistent kernel over all maps of the batch, so a map with an insert
+ * and a find in one batch sees its insert first.
+ *   ops_host: n_ops (<= 256) operations, at most one per (map, phase), on maps
+ *             of the batch's device with key_dim 1..4.  An insert on a map
+ *             with values needs exactly one value buffer of 4, 8 or 16-byte
+ *             rows, `values` aligned to the row size; other maps use
+ *             activate.  buf_indices is unused for erase.
+ *   Outputs and growth are as for the single-map calls (may synchronise to
+ *   grow a map).  The call returns after enqueueing; the batch context keeps
+ *   a ring of 4 descriptor slots and waits only when it reuses a slot whose
+ *   previous launch has not finished. */
+typedef struct ash_batch ash_batch;
+typedef enum ash_op { ASH_OP_INSERT = 0, ASH_OP_ACTIVATE = 1, ASH_OP_FIND = 2, ASH_OP_ERASE = 3 } ash_op;
+typedef struct ash_batch_op {
+  ash_map* map;
+  int32_t op;                /* ash_op */
+  int32_t pad;
+  const int32_t* keys;       /* [n, key_dim] */
+  const void* values;        /* insert only: [n] rows of the map's value buffer 0 */
+  int64_t n;
+  int32_t* buf_indices;      /* [n] out (insert, activate, find) */
+  uint8_t* masks;            /* [n] out */
+} ash_batch_op;
+ash_status ash_batch_create(int device, ash_batch** out_host);
+ash_status ash_batch_destroy(ash_batch* batch);
+ash_status ash_batch_run(ash_batch* batch, const ash_batch_op* ops_host, int n_ops, ash_stream stream);
+
+/* Autotuner: times activate + find on synthetic keys of this shape (n =
+ * min(capacity, 2^20) keys, uniqueness `rho` in (0, 1]) for candidate bucket
+ * sizes, table slots per unit of capacity and keys per thread, and writes the
+ * fastest tuning to *out_host.  Results are cached per (device, key_dim,
+ * capacity class, rho class).  Synchronises the stream. */
+ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int device, ash_stream stream,
+                        ash_tuning* out_host);
+
 /* Voxel quantisation (Sec. 6.1 listing; Eq. (10) with s*l as the cell edge):
  * keys[j] = floor(points[j] / cell) per coordinate, computed in float32 with
  * IEEE division and rounding toward minus infinity, for n_coords floats.

@@ -49,6 +49,14 @@ _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
 _lib = None
 
+ASH_OP_INSERT, ASH_OP_ACTIVATE, ASH_OP_FIND, ASH_OP_ERASE = range(4)
+
+
+class BatchOp(ctypes.Structure):
+    _fields_ = [("map", ctypes.c_void_p), ("op", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("buf_indices", ctypes.c_void_p), ("masks", ctypes.c_void_p)]
+
 # C signatures: name -> (restype, argtypes)
 _SIGS = {
     "ash_default_tuning": (None, [ctypes.POINTER(Tuning)]),
@@ -85,6 +93,10 @@ _SIGS = {
     "ash_trace_read": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "ash_trace_reset": (_I32, []),
     "ash_kernel_launch_count": (ctypes.c_uint64, []),
+    "ash_batch_create": (_I32, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "ash_batch_destroy": (_I32, [_P]),
+    "ash_batch_run": (_I32, [_P, ctypes.POINTER(BatchOp), ctypes.c_int, _P]),
+    "ash_autotune": (_I32, [ctypes.c_int, _I64, ctypes.c_float, ctypes.c_int, _P, ctypes.POINTER(Tuning)]),
     "ash_last_error": (ctypes.c_char_p, []),
 }
 
@@ -308,6 +320,63 @@ def ash_trace_collect():
 
 def ash_kernel_launch_count():
     return int(lib().ash_kernel_launch_count())
+
+
+def ash_autotune(key_dim, capacity, rho=1.0, device=0, stream=None) -> Tuning:
+    """Fastest tuning for maps of this shape (cached per shape class)."""
+    t = Tuning()
+    _check(lib().ash_autotune(int(key_dim), int(capacity), ctypes.c_float(rho), int(device),
+                              stream if stream is not None else _stream(device), ctypes.byref(t)))
+    return t
+
+
+def ash_batch_create(device=0):
+    h = ctypes.c_void_p()
+    _check(lib().ash_batch_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def ash_batch_destroy(handle):
+    _check(lib().ash_batch_destroy(handle))
+
+
+def ash_batch_run(handle, ops, stream=None):
+    """ops: sequence of BatchOp."""
+    arr = (BatchOp * max(1, len(ops)))(*ops)
+    _check(lib().ash_batch_run(handle, arr, len(ops), stream if stream is not None else _stream()))
+
+
+class Batch:
+    """One batched-execution context (a ring of CUDA graphs).  `run` takes
+    (HashMap, op, keys, values) tuples and returns [(buf_indices, masks)]."""
+
+    def __init__(self, device=0):
+        self.device = device
+        self._h = ash_batch_create(device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().ash_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def run(self, items, outputs=None):
+        ops, outs = [], []
+        for j, (hm, op, keys, values) in enumerate(items):
+            n = keys.shape[0]
+            if outputs is not None:
+                idx, mask = outputs[j]
+            else:
+                idx = torch.empty(n, dtype=torch.int32, device=keys.device) if op != ASH_OP_ERASE else None
+                mask = torch.empty(n, dtype=torch.bool, device=keys.device)
+            ops.append(BatchOp(hm.handle.value, op, 0, keys.data_ptr(), values.data_ptr() if values is not None else None,
+                               n, idx.data_ptr() if idx is not None else None, mask.data_ptr()))
+            outs.append((idx, mask))
+        ash_batch_run(self._h, ops)
+        return outs
 
 
 # -------------------------------------------------------------------- class

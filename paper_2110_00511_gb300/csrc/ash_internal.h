@@ -1,0 +1,87 @@
+// Internal host-side view of a map, shared by the translation units of the
+// library (map operations, batched execution, tuning, serving).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ash.h"
+#include "ash_kernels.cuh"
+
+namespace ash {
+namespace host {
+
+struct Allocator {
+  ash_alloc_fn alloc = nullptr;
+  ash_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+
+}  // namespace host
+}  // namespace ash
+
+struct ash_map {
+  int device = 0;
+  int key_dim = 0;
+  int ks = 0;  // key stride in kB
+  int n_values = 0;
+  int64_t capacity = 0;
+  int64_t n_slots = 0;
+  uint32_t n_buckets = 0;
+  int S = 4;
+  std::vector<int64_t> numel;
+  std::vector<int32_t> dtype;
+  std::vector<int64_t> row_bytes;
+  uint64_t* slots = nullptr;
+  int32_t* kb = nullptr;
+  int32_t* heap = nullptr;
+  std::vector<void*> vb;
+  ash::Ctrl* ctrl = nullptr;
+  ash::Ctrl* ctrl_host = nullptr;  // pinned mirror for synchronising reads
+  int32_t* scratch = nullptr;      // erase: one slot index per key
+  int64_t scratch_bytes = 0;
+  void* list_scratch = nullptr;    // listing: free-index bitmap + block counts
+  int64_t list_scratch_bytes = 0;
+  int64_t size_ub = 0;  // upper bound of live entries since the last sync
+  int64_t used_ub = 0;  // upper bound of used slots since the last sync
+  ash_tuning tuning{};
+  ash::DimKernels K{};
+  ash::host::Allocator alloc;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace ash {
+namespace host {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+ash_status fail(ash_status s, const std::string& msg);
+ash_status cuda_fail(cudaError_t e, const char* where);
+ash_status check_launch(const char* where);
+int sm_count(int device);
+int vec_width(int64_t row_bytes, const void* a, const void* b);
+void* dev_alloc(ash_map* m, size_t bytes, cudaStream_t st);
+void dev_free(ash_map* m, void* p, cudaStream_t st);
+Launch launch_of(const ash_map* m, cudaStream_t st);
+TableView view_of(const ash_map* m);
+ash_status check_keys(const ash_map* m, const void* keys, int64_t n);
+// x2 growth / table rebuild so that a batch of n insert keys fits (may synchronise st).
+ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st);
+
+}  // namespace host
+}  // namespace ash

@@ -344,6 +344,80 @@ __device__ __forceinline__ void copy_small_row(const ValueRow& v, int32_t i, int
 // (Sec. 4.3: t is raised by the number of indices taken).  Winners then write
 // kB(i), the value row, the committed slot word and their outputs.
 template <int D, int KPT, bool VAL>
+__device__ __forceinline__ void commit_tile(const TableView& t, const int32_t* __restrict__ keys, int64_t n,
+                                            int64_t base0, int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
+                                            const ValueRow& v, int* s_warp, int* s_base, int* s_got) {
+  const int64_t base = base0 + threadIdx.x;
+  int32_t s[KPT];
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+    s[q] = pos < n ? idx[pos] : -1;
+  }
+  uint64_t w[KPT];
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) w[q] = s[q] >= 0 ? load_slot_relaxed(t.slots + s[q]) : 0ull;
+  bool win[KPT];
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+    win[q] = s[q] >= 0 && lo32(w[q]) == (kClaimBit | static_cast<uint32_t>(pos));
+    cnt += win[q] ? 1 : 0;
+  }
+  int total;
+  const int off = block_exclusive_scan(cnt, total, s_warp);
+  if (threadIdx.x == 0) {
+    int got = 0, top = 0;
+    if (total > 0) {
+      const unsigned long long add = (static_cast<unsigned long long>(total) << 32) | static_cast<unsigned long long>(total);
+      const unsigned long long old = atomicAdd(&t.ctrl->top_used, add);
+      top = static_cast<int>(static_cast<uint32_t>(old));
+      got = t.capacity - top;
+      got = got < 0 ? 0 : (got > total ? total : got);
+      if (got < total) {
+        // give back the part of t that the heap could not serve
+        atomicAdd(&t.ctrl->top_used, 0ull - static_cast<unsigned long long>(total - got));
+        atomicOr(&t.ctrl->status, kStatusCapacity);
+      }
+    }
+    *s_base = top;
+    *s_got = got;
+  }
+  __syncthreads();
+  const int got = *s_got;
+  const int hbase = *s_base;
+  int r = off;
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+    if (pos < n) {
+      if (win[q]) {
+        if (r < got) {
+          const int32_t i = t.heap[hbase + r];
+          int32_t k[D];
+          load_input_key<D>(keys, pos, k);
+          store_kb<D>(t.kb, static_cast<uint32_t>(i), k);
+          if constexpr (VAL) copy_small_row(v, i, pos);
+          t.slots[s[q]] = (static_cast<uint64_t>(hi32(w[q])) << 32) | static_cast<uint32_t>(i);
+          idx[pos] = i;
+          mask[pos] = 1;
+        } else {
+          t.slots[s[q]] = kTombstone;
+          idx[pos] = -1;
+          mask[pos] = 0;
+        }
+        ++r;
+      } else {
+        idx[pos] = -1;
+        mask[pos] = 0;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int D, int KPT, bool VAL>
 __global__ void __launch_bounds__(256) commit_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
                                                      int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
                                                      ValueRow v) {
@@ -351,113 +425,97 @@ __global__ void __launch_bounds__(256) commit_kernel(TableView t, const int32_t*
   __shared__ int s_base;
   __shared__ int s_got;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
-  for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step) {
-    const int64_t base = base0 + threadIdx.x;
-    int32_t s[KPT];
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-      s[q] = pos < n ? idx[pos] : -1;
-    }
-    uint64_t w[KPT];
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) w[q] = s[q] >= 0 ? load_slot_relaxed(t.slots + s[q]) : 0ull;
-    bool win[KPT];
-    int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-      win[q] = s[q] >= 0 && lo32(w[q]) == (kClaimBit | static_cast<uint32_t>(pos));
-      cnt += win[q] ? 1 : 0;
-    }
-    int total;
-    const int off = block_exclusive_scan(cnt, total, s_warp);
-    if (threadIdx.x == 0) {
-      int got = 0, top = 0;
-      if (total > 0) {
-        const unsigned long long add = (static_cast<unsigned long long>(total) << 32) | static_cast<unsigned long long>(total);
-        const unsigned long long old = atomicAdd(&t.ctrl->top_used, add);
-        top = static_cast<int>(static_cast<uint32_t>(old));
-        got = t.capacity - top;
-        got = got < 0 ? 0 : (got > total ? total : got);
-        if (got < total) {
-          // give back the part of t that the heap could not serve
-          atomicAdd(&t.ctrl->top_used, 0ull - static_cast<unsigned long long>(total - got));
-          atomicOr(&t.ctrl->status, kStatusCapacity);
-        }
-      }
-      s_base = top;
-      s_got = got;
-    }
-    __syncthreads();
-    int r = off;
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-      if (pos < n) {
-        if (win[q]) {
-          if (r < s_got) {
-            const int32_t i = t.heap[s_base + r];
-            int32_t k[D];
-            load_input_key<D>(keys, pos, k);
-            store_kb<D>(t.kb, static_cast<uint32_t>(i), k);
-            if constexpr (VAL) copy_small_row(v, i, pos);
-            t.slots[s[q]] = (static_cast<uint64_t>(hi32(w[q])) << 32) | static_cast<uint32_t>(i);
-            idx[pos] = i;
-            mask[pos] = 1;
-          } else {
-            t.slots[s[q]] = kTombstone;
-            idx[pos] = -1;
-            mask[pos] = 0;
-          }
-          ++r;
-        } else {
-          idx[pos] = -1;
-          mask[pos] = 0;
-        }
-      }
-    }
-    __syncthreads();
-  }
+  for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step)
+    commit_tile<D, KPT, VAL>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
 }
 
 // --------------------------------------------------------------- erase: mark
+// Finds input row pos and marks its slot with the lowest position seen
+// (atomicMin into the high word, the buffer index kept in the low word).
+// Returns the slot index, or -1 if the key is absent.
+template <int D, int S>
+__device__ __forceinline__ int32_t erase_mark_one(const TableView& t, const int32_t* __restrict__ keys, int64_t pos) {
+  int32_t k[D];
+  load_input_key<D>(keys, pos, k);
+  const uint64_t h = hash_key<D>(k);
+  const uint32_t fp = fingerprint(h);
+  uint32_t b = home_bucket(h, t.n_buckets);
+  int32_t res = -1;
+  for (uint32_t probe = 0; probe < t.max_probes && res < 0; ++probe) {
+    uint64_t* bp = t.slots + static_cast<size_t>(b) * S;
+    uint64_t w[S];
+    load_bucket<S, false>(bp, w);
+    bool stop = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      stop |= (w[s] == kEmpty);
+      const uint32_t lo = lo32(w[s]), hi = hi32(w[s]);
+      // committed with an equal fingerprint, or already marked (fingerprint gone)
+      if (res < 0 && lo < kClaimBit && (hi == fp || hi < kFpBit) && kb_equal<D>(t.kb, lo, k)) {
+        if (hi > static_cast<uint32_t>(pos))
+          atomicMin(reinterpret_cast<unsigned long long*>(bp + s), (static_cast<unsigned long long>(pos) << 32) | lo);
+        res = static_cast<int32_t>(b * S + s);
+      }
+    }
+    if (stop) break;
+    b = next_bucket(b, t.n_buckets);
+  }
+  return res;
+}
+
 template <int D, int S>
 __global__ void __launch_bounds__(256) erase_mark_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
                                                          int32_t* __restrict__ slot_out) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; pos < n; pos += stride) {
-    int32_t k[D];
-    load_input_key<D>(keys, pos, k);
-    const uint64_t h = hash_key<D>(k);
-    const uint32_t fp = fingerprint(h);
-    uint32_t b = home_bucket(h, t.n_buckets);
-    int32_t res = -1;
-    for (uint32_t probe = 0; probe < t.max_probes && res < 0; ++probe) {
-      uint64_t* bp = t.slots + static_cast<size_t>(b) * S;
-      uint64_t w[S];
-      load_bucket<S, false>(bp, w);
-      bool stop = false;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        stop |= (w[s] == kEmpty);
-        const uint32_t lo = lo32(w[s]), hi = hi32(w[s]);
-        // committed with an equal fingerprint, or already marked (fingerprint gone)
-        if (res < 0 && lo < kClaimBit && (hi == fp || hi < kFpBit) && kb_equal<D>(t.kb, lo, k)) {
-          if (hi > static_cast<uint32_t>(pos))
-            atomicMin(reinterpret_cast<unsigned long long*>(bp + s),
-                      (static_cast<unsigned long long>(pos) << 32) | lo);
-          res = static_cast<int32_t>(b * S + s);
-        }
-      }
-      if (stop) break;
-      b = next_bucket(b, t.n_buckets);
-    }
-    slot_out[pos] = res;
-  }
+  for (int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; pos < n; pos += stride)
+    slot_out[pos] = erase_mark_one<D, S>(t, keys, pos);
 }
 
 // ------------------------------------------------------------ erase: resolve
+// One tile of blockDim.x positions starting at base0.  Every thread of the
+// block must call it (block-wide scan and barriers).
+template <int S>
+__device__ __forceinline__ void erase_resolve_tile(const TableView& t, int64_t n, int64_t base0,
+                                                   const int32_t* __restrict__ slot_in, uint8_t* __restrict__ mask,
+                                                   int* s_warp, int* s_cnt, int* s_base) {
+  const int64_t pos = base0 + threadIdx.x;
+  const bool active = pos < n;
+  const int32_t s = active ? slot_in[pos] : -1;
+  uint64_t w = 0;
+  bool win = false, to_empty = false;
+  if (s >= 0) {
+    w = load_slot_relaxed(t.slots + s);
+    win = hi32(w) == static_cast<uint32_t>(pos);
+    if (win) {
+      uint64_t bw[S];
+      load_bucket<S, false>(t.slots + static_cast<size_t>(s / S) * S, bw);
+#pragma unroll
+      for (int q = 0; q < S; ++q) to_empty |= (bw[q] == kEmpty);
+    }
+  }
+  int rank, total;
+  block_rank(win, rank, total, s_warp);
+  const int n_empty = block_count(to_empty, s_cnt);
+  if (threadIdx.x == 0) {
+    int top = 0;
+    if (total > 0) {
+      const unsigned long long sub = (static_cast<unsigned long long>(n_empty) << 32) + static_cast<unsigned long long>(total);
+      const unsigned long long old = atomicAdd(&t.ctrl->top_used, 0ull - sub);
+      top = static_cast<int>(static_cast<uint32_t>(old));
+    }
+    *s_base = top - total;
+  }
+  __syncthreads();
+  if (win) {
+    t.heap[*s_base + rank] = static_cast<int32_t>(lo32(w));
+    t.slots[s] = to_empty ? kEmpty : kTombstone;
+    mask[pos] = 1;
+  } else if (active) {
+    mask[pos] = 0;
+  }
+  __syncthreads();
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) erase_resolve_kernel(TableView t, int64_t n, const int32_t* __restrict__ slot_in,
                                                             uint8_t* __restrict__ mask) {
@@ -465,44 +523,8 @@ __global__ void __launch_bounds__(256) erase_resolve_kernel(TableView t, int64_t
   __shared__ int s_cnt;
   __shared__ int s_base;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
-    const int64_t pos = base + threadIdx.x;
-    const bool active = pos < n;
-    const int32_t s = active ? slot_in[pos] : -1;
-    uint64_t w = 0;
-    bool win = false, to_empty = false;
-    if (s >= 0) {
-      w = load_slot_relaxed(t.slots + s);
-      win = hi32(w) == static_cast<uint32_t>(pos);
-      if (win) {
-        uint64_t bw[S];
-        load_bucket<S, false>(t.slots + static_cast<size_t>(s / S) * S, bw);
-#pragma unroll
-        for (int q = 0; q < S; ++q) to_empty |= (bw[q] == kEmpty);
-      }
-    }
-    int rank, total;
-    block_rank(win, rank, total, s_warp);
-    const int n_empty = block_count(to_empty, &s_cnt);
-    if (threadIdx.x == 0) {
-      int top = 0;
-      if (total > 0) {
-        const unsigned long long sub = (static_cast<unsigned long long>(n_empty) << 32) + static_cast<unsigned long long>(total);
-        const unsigned long long old = atomicAdd(&t.ctrl->top_used, 0ull - sub);
-        top = static_cast<int>(static_cast<uint32_t>(old));
-      }
-      s_base = top - total;
-    }
-    __syncthreads();
-    if (win) {
-      t.heap[s_base + rank] = static_cast<int32_t>(lo32(w));
-      t.slots[s] = to_empty ? kEmpty : kTombstone;
-      mask[pos] = 1;
-    } else if (active) {
-      mask[pos] = 0;
-    }
-    __syncthreads();
-  }
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride)
+    erase_resolve_tile<S>(t, n, base, slot_in, mask, s_warp, &s_cnt, &s_base);
 }
 
 // ------------------------------------------------------------------ rebuild

@@ -18,9 +18,11 @@
 
 #include "ash.h"
 #include "ash_aux.h"
+#include "ash_internal.h"
 #include "ash_kernels.cuh"
 
-namespace {
+namespace ash {
+namespace host {
 
 thread_local std::string g_last_error;
 
@@ -39,11 +41,7 @@ ash_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-struct Allocator {
-  ash_alloc_fn alloc = nullptr;
-  ash_free_fn free = nullptr;
-  void* ctx = nullptr;
-};
+
 
 std::mutex g_mu;
 Allocator g_alloc;
@@ -98,19 +96,7 @@ int sm_count(int device) {
   return cache[device];
 }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
+
 
 int vec_width(int64_t row_bytes, const void* a, const void* b) {
   const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b);
@@ -120,39 +106,6 @@ int vec_width(int64_t row_bytes, const void* a, const void* b) {
   return 1;
 }
 
-}  // namespace
-
-struct ash_map {
-  int device = 0;
-  int key_dim = 0;
-  int ks = 0;  // key stride in kB
-  int n_values = 0;
-  int64_t capacity = 0;
-  int64_t n_slots = 0;
-  uint32_t n_buckets = 0;
-  int S = 4;
-  std::vector<int64_t> numel;
-  std::vector<int32_t> dtype;
-  std::vector<int64_t> row_bytes;
-  uint64_t* slots = nullptr;
-  int32_t* kb = nullptr;
-  int32_t* heap = nullptr;
-  std::vector<void*> vb;
-  ash::Ctrl* ctrl = nullptr;
-  ash::Ctrl* ctrl_host = nullptr;  // pinned mirror for synchronising reads
-  int32_t* scratch = nullptr;      // erase: one slot index per key
-  int64_t scratch_bytes = 0;
-  void* list_scratch = nullptr;    // listing: free-index bitmap + block counts
-  int64_t list_scratch_bytes = 0;
-  int64_t size_ub = 0;  // upper bound of live entries since the last sync
-  int64_t used_ub = 0;  // upper bound of used slots since the last sync
-  ash_tuning tuning{};
-  ash::DimKernels K{};
-  Allocator alloc;
-  cudaStream_t last_stream = nullptr;
-};
-
-namespace {
 
 void* dev_alloc(ash_map* m, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 256;
@@ -509,7 +462,10 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   return check_launch("insert");
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace ash
+
+using namespace ash::host;
 
 extern "C" {
 

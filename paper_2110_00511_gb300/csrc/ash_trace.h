@@ -20,6 +20,8 @@ enum KernelKind {
   kKQuantize,
   kKProbe,
   kKSetCtrl,
+  kKBatch,
+  kKSynthKeys,
   kKernelKinds
 };
 
