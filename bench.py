@@ -47,6 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--ops-n", type=int, default=10_000_000)
     p.add_argument("--lean", action="store_true", help="timed steps only (no probe, e2e, per-op or cpu legs)")
+    p.add_argument("--no-batched", action="store_true", help="skip the many-map batched comparison")
+    p.add_argument("--batched-maps", type=int, default=64)
     return p.parse_args(argv)
 
 
@@ -447,6 +449,10 @@ def main(argv=None):
     if not args.no_ops and not args.lean:
         ops = per_op_figures(args, device, hbm_peak)
 
+    batched = None
+    if not args.no_batched and not args.lean:
+        batched = batched_figures(args, device)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.lean:
         cpu = cpu_baseline(args, pts_np)
@@ -463,7 +469,7 @@ def main(argv=None):
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "kernels": kernels, "random_read_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "source_digest": source_digest()}
+                "ops": ops, "batched": batched, "source_digest": source_digest()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -565,6 +571,70 @@ def per_op_figures(args, device, hbm_peak):
     rec("rehash_x2", ms_rh, rh_bytes, n_unique)
     del hm
     return out
+
+
+def batched_figures(args, device, reps=15):
+    """Many maps, one mixed batch each (key_dim 2-4, capacities log-uniform in
+    2^10..2^21, 30/60/10 insert/find/erase, rho ~ U(0.2, 1)), serviced (a) as
+    ONE graph launch of the batched kernels and (b) as plain per-map calls
+    (insert, find, erase for each map) through the same binding.  Maps are
+    cleared between repetitions (untimed); each repetition is timed with CUDA
+    events around the whole service."""
+    import torch
+    from paper_2110_00511_gb300 import ash, workloads
+    cases = workloads.batched_maps(n_maps=args.batched_maps, seed=0)
+    tunings = [ash.ash_autotune(c.key_dim, c.capacity, c.rho, device.index) for c in cases]
+    dev_data = [(torch.from_numpy(c.insert_keys).to(device), torch.from_numpy(c.insert_values).to(device),
+                 torch.from_numpy(c.find_keys).to(device), torch.from_numpy(c.erase_keys).to(device)) for c in cases]
+    n_ops = sum(len(c.insert_keys) + len(c.find_keys) + len(c.erase_keys) for c in cases)
+
+    def make_maps():
+        return [ash.HashMap(c.key_dim, c.capacity, [(1,)], [torch.float32], device=device, tuning=t)
+                for c, t in zip(cases, tunings)]
+
+    maps_b, maps_p = make_maps(), make_maps()
+    batch = ash.Batch(device.index)
+    items = []
+    outputs = []
+    for hm, (ik, iv, fk, ek) in zip(maps_b, dev_data):
+        items += [(hm, ash.ASH_OP_INSERT, ik, iv), (hm, ash.ASH_OP_FIND, fk, None), (hm, ash.ASH_OP_ERASE, ek, None)]
+        outputs += [(torch.empty(len(ik), dtype=torch.int32, device=device), torch.empty(len(ik), dtype=torch.bool, device=device)),
+                    (torch.empty(len(fk), dtype=torch.int32, device=device), torch.empty(len(fk), dtype=torch.bool, device=device)),
+                    (None, torch.empty(len(ek), dtype=torch.bool, device=device))]
+
+    def run_batched():
+        batch.run(items, outputs)
+
+    def run_plain():
+        for hm, (ik, iv, fk, ek) in zip(maps_p, dev_data):
+            hm.insert(ik, [iv])
+            hm.find(fk)
+            hm.erase(ek)
+
+    res = {}
+    for name, fn, maps in (("batched_graph", run_batched, maps_b), ("plain_per_map", run_plain, maps_p)):
+        times = []
+        for r in range(reps + 2):
+            for hm in maps:
+                hm.clear()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                times.append(e0.elapsed_time(e1))
+        times_sorted = sorted(times)
+        res[name] = {"ms_median": statistics.median(times),
+                     "ms_p99": times_sorted[min(len(times) - 1, int(0.99 * len(times)))],
+                     "ops_per_s": n_ops / (statistics.median(times) / 1000.0)}
+    res["maps"] = len(cases)
+    res["ops_per_batch"] = n_ops
+    res["speedup_ops_per_s"] = res["batched_graph"]["ops_per_s"] / res["plain_per_map"]["ops_per_s"]
+    res["timing"] = ("CUDA events on the stream around the whole service of all maps' batches (the plain "
+                     "form's span includes GPU idle time while the host issues its calls)")
+    return res
 
 
 if __name__ == "__main__":

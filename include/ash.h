@@ -250,6 +250,55 @@ ash_status ash_batch_run(ash_batch* batch, const ash_batch_op* ops_host, int n_o
 ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int device, ash_stream stream,
                         ash_tuning* out_host);
 
+/* ---------------------------------------------------------------------------
+ * Multi-tenant serving with continuous batching (no counterpart in the paper;
+ * it serves the per-map operations above to many clients).  Tenant maps stay
+ * resident.  ash_server_submit copies a request's keys (and values) from host
+ * memory into pinned staging and queues it; a worker thread admits queued
+ * requests in arrival order while their device staging fits staging_bytes,
+ * batches at most one request per tenant (so each tenant's requests apply in
+ * arrival order), grows a tenant map x2 before an insert would push its
+ * live/capacity ratio past max_load, and runs each batch as one
+ * ash_batch_run graph between an upload and a download on separate streams.
+ * Requests that arrive while batches are on the GPU join the next batch.
+ *   ash_server_wait: blocks until the request's outputs are on the host,
+ *     copies them to the caller's buf_indices/masks (given at submit; they
+ *     must stay valid until then) and returns the latency from submit to
+ *     outputs on the host.  timeout_ms < 0 waits forever; a timeout returns
+ *     ASH_ERR_TIMEOUT and the request can be waited for again.
+ *   ash_server_map / ash_server_stream: a tenant map and the stream its
+ *     kernels run on, for inspection after all submitted requests were
+ *     waited for.
+ *   ash_server_destroy: finishes queued requests, then frees everything. */
+typedef struct ash_server ash_server;
+typedef struct ash_server_config {
+  int32_t n_tenants;          /* 1..256 resident maps */
+  int32_t key_dim;            /* 1..4 */
+  int64_t initial_capacity;   /* per tenant */
+  int32_t value_row_bytes;    /* 0 (hash sets) or 4, 8, 16: one value buffer */
+  int32_t device;
+  int64_t staging_bytes;      /* HBM budget for admitted requests' device buffers */
+  float max_load;             /* grow before live/capacity would pass this (0.7) */
+  int32_t max_batch_requests; /* requests per batch, 1..256 */
+} ash_server_config;
+typedef struct ash_server_stats {
+  int64_t submitted;
+  int64_t completed;
+  int64_t batches;
+  int64_t batched_requests;
+  int64_t rehashes;
+} ash_server_stats;
+void ash_server_default_config(ash_server_config* out);
+ash_status ash_server_create(const ash_server_config* cfg_host, ash_server** out_host);
+ash_status ash_server_destroy(ash_server* server);
+ash_status ash_server_submit(ash_server* server, int32_t tenant, int32_t op, const int32_t* keys_host,
+                             const void* values_host, int64_t n, int32_t* buf_indices_host, uint8_t* masks_host,
+                             uint64_t* request_id_host);
+ash_status ash_server_wait(ash_server* server, uint64_t request_id, int64_t timeout_ms, double* latency_ms_host);
+ash_status ash_server_stats_get(ash_server* server, ash_server_stats* out_host);
+ash_status ash_server_map(ash_server* server, int32_t tenant, ash_map** out_host);
+ash_status ash_server_stream(ash_server* server, ash_stream* out_host);
+
 /* Voxel quantisation (Sec. 6.1 listing; Eq. (10) with s*l as the cell edge):
  * keys[j] = floor(points[j] / cell) per coordinate, computed in float32 with
  * IEEE division and rounding toward minus infinity, for n_coords floats.

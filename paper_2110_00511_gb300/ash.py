@@ -52,6 +52,20 @@ _lib = None
 ASH_OP_INSERT, ASH_OP_ACTIVATE, ASH_OP_FIND, ASH_OP_ERASE = range(4)
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_tenants", ctypes.c_int32), ("key_dim", ctypes.c_int32), ("initial_capacity", ctypes.c_int64),
+                ("value_row_bytes", ctypes.c_int32), ("device", ctypes.c_int32), ("staging_bytes", ctypes.c_int64),
+                ("max_load", ctypes.c_float), ("max_batch_requests", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64), ("rehashes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BatchOp(ctypes.Structure):
     _fields_ = [("map", ctypes.c_void_p), ("op", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_int64),
@@ -97,6 +111,14 @@ _SIGS = {
     "ash_batch_destroy": (_I32, [_P]),
     "ash_batch_run": (_I32, [_P, ctypes.POINTER(BatchOp), ctypes.c_int, _P]),
     "ash_autotune": (_I32, [ctypes.c_int, _I64, ctypes.c_float, ctypes.c_int, _P, ctypes.POINTER(Tuning)]),
+    "ash_server_default_config": (None, [ctypes.POINTER(ServerConfig)]),
+    "ash_server_create": (_I32, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    "ash_server_destroy": (_I32, [_P]),
+    "ash_server_submit": (_I32, [_P, _I32, _I32, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "ash_server_wait": (_I32, [_P, ctypes.c_uint64, _I64, ctypes.POINTER(ctypes.c_double)]),
+    "ash_server_stats_get": (_I32, [_P, ctypes.POINTER(ServerStats)]),
+    "ash_server_map": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
+    "ash_server_stream": (_I32, [_P, ctypes.POINTER(_P)]),
     "ash_last_error": (ctypes.c_char_p, []),
 }
 
@@ -379,6 +401,70 @@ class Batch:
         return outs
 
 
+def ash_server_default_config() -> ServerConfig:
+    c = ServerConfig()
+    lib().ash_server_default_config(ctypes.byref(c))
+    return c
+
+
+class Server:
+    """Multi-tenant continuous-batching server (native worker thread).
+
+    submit() takes host numpy arrays and returns a request id; wait(id)
+    returns (buf_indices, masks, latency_ms) as numpy arrays."""
+
+    def __init__(self, config=None, **kw):
+        cfg = config or ash_server_default_config()
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        self._h = ctypes.c_void_p()
+        _check(lib().ash_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._live = {}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(lib().ash_server_destroy(self._h))
+        self._h = None
+        self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, tenant, op, keys, values=None):
+        import numpy as np
+        keys = np.ascontiguousarray(keys, dtype=np.int32)
+        n = keys.shape[0]
+        vals = None if values is None else np.ascontiguousarray(values)
+        idx = np.empty(n, np.int32)
+        mask = np.empty(n, np.uint8)
+        rid = ctypes.c_uint64()
+        _check(lib().ash_server_submit(self._h, int(tenant), int(op), keys.ctypes.data,
+                                       vals.ctypes.data if vals is not None else None, n,
+                                       idx.ctypes.data, mask.ctypes.data, ctypes.byref(rid)))
+        self._live[rid.value] = (keys, vals, idx, mask)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1):
+        lat = ctypes.c_double()
+        _check(lib().ash_server_wait(self._h, ctypes.c_uint64(rid), int(timeout_ms), ctypes.byref(lat)))
+        keys, vals, idx, mask = self._live.pop(rid)
+        return idx, mask.astype(bool), lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().ash_server_stats_get(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def map_handle(self, tenant):
+        h = ctypes.c_void_p()
+        _check(lib().ash_server_map(self._h, int(tenant), ctypes.byref(h)))
+        return h
+
+
 # -------------------------------------------------------------------- class
 class HashMap:
     """A GPU hash map with int32 keys of dimension key_dim and SoA value
@@ -397,9 +483,21 @@ class HashMap:
         self._h = ash_create(self.key_dim, capacity, numel, self.value_dtypes, self.device.index, tuning,
                              _stream(self.device))
 
+    @classmethod
+    def wrap(cls, handle, key_dim, value_shapes=(), value_dtypes=(), device=0):
+        """A non-owning view of a map created elsewhere (e.g. a server tenant)."""
+        self = cls.__new__(cls)
+        self.device = torch.device("cuda", device)
+        self.key_dim = int(key_dim)
+        self.value_shapes = [tuple(s if isinstance(s, (tuple, list)) else (s,)) for s in value_shapes]
+        self.value_dtypes = list(value_dtypes)
+        self._h = handle
+        self._owned = False
+        return self
+
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value:
+        if h is not None and h.value and getattr(self, "_owned", True):
             try:
                 lib().ash_destroy(h)
             except Exception:

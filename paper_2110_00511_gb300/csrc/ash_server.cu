@@ -1,0 +1,453 @@
+// Multi-tenant serving with continuous batching.
+//
+// Tenant maps stay resident on the device.  Requests (one operation on one
+// tenant: insert, activate, find or erase of n keys) arrive through
+// ash_server_submit, which copies the caller's keys and values into pinned
+// staging and queues the request.  A worker thread repeatedly
+//   1. releases the device staging of batches that finished,
+//   2. admits queued requests in arrival order while their device staging
+//      fits the HBM budget (a request larger than the whole budget is admitted
+//      alone),
+//   3. forms a batch of at most one admitted request per tenant (so each
+//      tenant's requests run in arrival order), grows a tenant map x2 before
+//      an insert would push its live/capacity ratio past max_load,
+//   4. uploads the batch on a copy stream, runs it as ONE ash_batch_run graph
+//      on the compute stream, downloads its outputs on a second copy stream
+//      and marks the requests done from a host callback.
+// The worker does not wait for a batch before launching the next one, so
+// uploads, kernels and downloads of consecutive batches overlap, and requests
+// that arrive while others are on the GPU join the next batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ash.h"
+#include "ash_internal.h"
+
+using namespace ash::host;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+constexpr int kMaxTenants = 256;
+
+int64_t align256(int64_t x) { return (x + 255) & ~int64_t{255}; }
+
+// Pinned host blocks recycled by power-of-two size class.
+class PinnedPool {
+ public:
+  void* take(int64_t bytes, int64_t* cls_bytes) {
+    int64_t c = 4096;
+    while (c < bytes) c <<= 1;
+    *cls_bytes = c;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      auto& v = free_[c];
+      if (!v.empty()) {
+        void* p = v.back();
+        v.pop_back();
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void give(void* p, int64_t cls_bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    free_[cls_bytes].push_back(p);
+  }
+  ~PinnedPool() {
+    for (auto& kv : free_)
+      for (void* p : kv.second) cudaFreeHost(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::map<int64_t, std::vector<void*>> free_;
+};
+
+struct Request {
+  uint64_t id = 0;
+  int tenant = 0;
+  int op = 0;
+  int64_t n = 0;
+  int32_t* idx_user = nullptr;
+  uint8_t* mask_user = nullptr;
+  // staging: [keys | values | idx | mask], each 256-byte aligned
+  int64_t off_keys = 0, off_vals = 0, off_idx = 0, off_mask = 0, bytes = 0;
+  void* host = nullptr;
+  int64_t host_cls = 0;
+  char* dev = nullptr;
+  Clock::time_point t_submit, t_done;
+  bool gpu_done = false;
+  bool delivered = false;
+};
+
+struct Batch {
+  std::vector<Request*> reqs;
+  struct ash_server* server = nullptr;
+  bool done = false;
+};
+
+}  // namespace
+
+struct ash_server {
+  ash_server_config cfg{};
+  std::vector<ash_map*> maps;
+  ash_batch* batch = nullptr;
+  cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+  PinnedPool pinned;
+  int64_t value_bytes = 0;
+
+  std::mutex mu;
+  std::condition_variable cv_work;
+  std::condition_variable cv_done;
+  std::deque<Request*> pending;   // submitted, not yet admitted
+  std::deque<Request*> admitted;  // device staging granted, not yet launched
+  std::deque<Batch*> inflight;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  int64_t staged_bytes = 0;       // device staging held by admitted / in-flight requests
+  uint64_t next_id = 1;
+  bool stop = false;
+  ash_status worker_error = ASH_OK;
+  std::thread worker;
+  ash_server_stats stats{};
+};
+
+namespace {
+
+void CUDART_CB on_batch_done(void* arg) {
+  Batch* b = static_cast<Batch*>(arg);
+  ash_server* s = b->server;
+  const auto now = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (Request* r : b->reqs) {
+      r->t_done = now;
+      r->gpu_done = true;
+    }
+    b->done = true;
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_one();
+}
+
+// Worker-side: grow tenant maps so that an insert of n keys keeps the live /
+// capacity ratio at or below max_load (synchronises the compute stream).
+ash_status grow_for_insert(ash_server* s, ash_map* m, int64_t n) {
+  const double lim = s->cfg.max_load;
+  if (static_cast<double>(m->size_ub + n) <= lim * static_cast<double>(m->capacity)) return ASH_OK;
+  int64_t size = 0;
+  ash_status st = ash_size(m, &size, reinterpret_cast<ash_stream>(s->s_comp));
+  if (st != ASH_OK) return st;
+  int64_t c = m->capacity;
+  while (static_cast<double>(size + n) > lim * static_cast<double>(c)) c *= 2;
+  if (c != m->capacity) {
+    st = ash_reserve(m, c, reinterpret_cast<ash_stream>(s->s_comp));
+    if (st != ASH_OK) return st;
+    s->stats.rehashes += 1;
+  }
+  return ASH_OK;
+}
+
+void worker_loop(ash_server* s) {
+  DeviceGuard g(s->cfg.device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // 1) release the device staging of finished batches (in order)
+    while (!s->inflight.empty() && s->inflight.front()->done) {
+      Batch* b = s->inflight.front();
+      s->inflight.pop_front();
+      for (Request* r : b->reqs) {
+        cudaFreeAsync(r->dev, s->s_d2h);
+        r->dev = nullptr;
+        s->staged_bytes -= r->bytes;
+      }
+      delete b;
+    }
+    if (s->stop && s->pending.empty() && s->admitted.empty() && s->inflight.empty()) break;
+    // 2) admission under the HBM staging budget, in arrival order
+    while (!s->pending.empty()) {
+      Request* r = s->pending.front();
+      const bool alone = s->staged_bytes == 0;
+      if (!alone && s->staged_bytes + r->bytes > s->cfg.staging_bytes) break;
+      s->pending.pop_front();
+      s->staged_bytes += r->bytes;
+      s->admitted.push_back(r);
+    }
+    // 3) a batch: the oldest admitted request of each tenant
+    std::vector<Request*> pick;
+    {
+      bool used[kMaxTenants] = {};
+      for (auto it = s->admitted.begin(); it != s->admitted.end() && static_cast<int>(pick.size()) < s->cfg.max_batch_requests;) {
+        Request* r = *it;
+        if (!used[r->tenant]) {
+          used[r->tenant] = true;
+          pick.push_back(r);
+          it = s->admitted.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    if (pick.empty()) {
+      s->cv_work.wait(lk);
+      continue;
+    }
+    lk.unlock();
+    // 4) launch: upload, one batched graph, download, host callback
+    ash_status st = ASH_OK;
+    std::vector<ash_batch_op> ops;
+    for (Request* r : pick) {
+      if (r->op == ASH_OP_INSERT || r->op == ASH_OP_ACTIVATE) {
+        st = grow_for_insert(s, s->maps[r->tenant], r->n);
+        if (st != ASH_OK) break;
+      }
+    }
+    if (st == ASH_OK) {
+      for (Request* r : pick) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, s->s_h2d) != cudaSuccess) {
+          cudaGetLastError();
+          st = ASH_ERR_OOM;
+          break;
+        }
+        const int64_t in_bytes = r->off_idx;  // keys and values precede the outputs
+        cudaMemcpyAsync(r->dev, r->host, in_bytes, cudaMemcpyHostToDevice, s->s_h2d);
+        ash_batch_op o{};
+        o.map = s->maps[r->tenant];
+        o.op = r->op;
+        o.keys = reinterpret_cast<const int32_t*>(r->dev + r->off_keys);
+        o.values = (r->op == ASH_OP_INSERT && s->value_bytes > 0) ? r->dev + r->off_vals : nullptr;
+        o.n = r->n;
+        o.buf_indices = reinterpret_cast<int32_t*>(r->dev + r->off_idx);
+        o.masks = reinterpret_cast<uint8_t*>(r->dev + r->off_mask);
+        ops.push_back(o);
+      }
+    }
+    if (st == ASH_OK) {
+      cudaEvent_t up, comp;
+      cudaEventCreateWithFlags(&up, cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&comp, cudaEventDisableTiming);
+      cudaEventRecord(up, s->s_h2d);
+      cudaStreamWaitEvent(s->s_comp, up, 0);
+      st = ash_batch_run(s->batch, ops.data(), static_cast<int>(ops.size()), reinterpret_cast<ash_stream>(s->s_comp));
+      cudaEventRecord(comp, s->s_comp);
+      cudaStreamWaitEvent(s->s_d2h, comp, 0);
+      for (Request* r : pick) {
+        const int64_t out_bytes = r->bytes - r->off_idx;
+        cudaMemcpyAsync(static_cast<char*>(r->host) + r->off_idx, r->dev + r->off_idx, out_bytes,
+                        cudaMemcpyDeviceToHost, s->s_d2h);
+      }
+      cudaEventDestroy(up);
+      cudaEventDestroy(comp);
+      Batch* b = new Batch();
+      b->reqs = pick;
+      b->server = s;
+      lk.lock();
+      s->inflight.push_back(b);
+      s->stats.batches += 1;
+      s->stats.batched_requests += static_cast<int64_t>(pick.size());
+      lk.unlock();
+      if (cudaLaunchHostFunc(s->s_d2h, on_batch_done, b) != cudaSuccess) st = ASH_ERR_CUDA;
+    }
+    lk.lock();
+    if (st != ASH_OK) {
+      // fail the picked requests so no waiter hangs, and give back their staging
+      s->worker_error = st;
+      for (Request* r : pick) {
+        if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
+        r->dev = nullptr;
+        s->staged_bytes -= r->bytes;
+        r->gpu_done = true;
+        r->t_done = Clock::now();
+      }
+      s->cv_done.notify_all();
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void ash_server_default_config(ash_server_config* c) {
+  if (!c) return;
+  c->n_tenants = 16;
+  c->key_dim = 3;
+  c->initial_capacity = 1 << 20;
+  c->value_row_bytes = 0;
+  c->device = 0;
+  c->staging_bytes = int64_t{2} << 30;
+  c->max_load = 0.7f;
+  c->max_batch_requests = 256;
+}
+
+ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host) {
+  if (!cfg || !out_host) return fail(ASH_ERR_INVALID, "config and out are required");
+  *out_host = nullptr;
+  if (cfg->n_tenants < 1 || cfg->n_tenants > kMaxTenants) return fail(ASH_ERR_INVALID, "n_tenants must be in 1..256");
+  if (cfg->key_dim < 1 || cfg->key_dim > 4) return fail(ASH_ERR_INVALID, "key_dim must be in 1..4");
+  if (!(cfg->value_row_bytes == 0 || cfg->value_row_bytes == 4 || cfg->value_row_bytes == 8 || cfg->value_row_bytes == 16))
+    return fail(ASH_ERR_INVALID, "value_row_bytes must be 0, 4, 8 or 16");
+  if (cfg->initial_capacity < 1 || cfg->staging_bytes < (1 << 20)) return fail(ASH_ERR_INVALID, "bad capacity or budget");
+  if (!(cfg->max_load > 0.05f && cfg->max_load <= 1.0f)) return fail(ASH_ERR_INVALID, "max_load must be in (0.05, 1]");
+  if (cfg->max_batch_requests < 1 || cfg->max_batch_requests > 256) return fail(ASH_ERR_INVALID, "max_batch_requests in 1..256");
+  std::unique_ptr<ash_server> s(new ash_server());
+  s->cfg = *cfg;
+  s->value_bytes = cfg->value_row_bytes;
+  DeviceGuard g(cfg->device);
+  if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "server streams");
+  ash_status st = ash_batch_create(cfg->device, &s->batch);
+  if (st != ASH_OK) return st;
+  const int64_t numel = cfg->value_row_bytes / 4;
+  const int32_t dt = ASH_I32;
+  for (int t = 0; t < cfg->n_tenants; ++t) {
+    ash_map* m = nullptr;
+    st = ash_create(cfg->key_dim, cfg->initial_capacity, cfg->value_row_bytes ? 1 : 0, &numel, &dt, cfg->device, nullptr,
+                    reinterpret_cast<ash_stream>(s->s_comp), &m);
+    if (st != ASH_OK) {
+      for (ash_map* x : s->maps) ash_destroy(x);
+      ash_batch_destroy(s->batch);
+      return st;
+    }
+    s->maps.push_back(m);
+  }
+  cudaStreamSynchronize(s->s_comp);
+  ash_server* raw = s.release();
+  raw->worker = std::thread(worker_loop, raw);
+  *out_host = raw;
+  return ASH_OK;
+}
+
+ash_status ash_server_submit(ash_server* s, int32_t tenant, int32_t op, const int32_t* keys_host,
+                             const void* values_host, int64_t n, int32_t* buf_indices_host, uint8_t* masks_host,
+                             uint64_t* request_id_host) {
+  if (!s || !request_id_host) return fail(ASH_ERR_INVALID, "server and request_id are required");
+  if (tenant < 0 || tenant >= s->cfg.n_tenants) return fail(ASH_ERR_INVALID, "tenant out of range");
+  if (op < ASH_OP_INSERT || op > ASH_OP_ERASE) return fail(ASH_ERR_INVALID, "unknown op");
+  if (n < 1 || n >= 0x7FFFFFFF) return fail(ASH_ERR_INVALID, "n must be in [1, 2^31 - 1)");
+  if (!keys_host || !masks_host) return fail(ASH_ERR_INVALID, "keys and masks are required");
+  if (op != ASH_OP_ERASE && !buf_indices_host) return fail(ASH_ERR_INVALID, "buf_indices is required");
+  if (op == ASH_OP_INSERT && s->value_bytes > 0 && !values_host) return fail(ASH_ERR_INVALID, "values are required");
+  auto r = std::make_unique<Request>();
+  r->tenant = tenant;
+  r->op = op;
+  r->n = n;
+  r->idx_user = buf_indices_host;
+  r->mask_user = masks_host;
+  const int64_t kb = n * s->cfg.key_dim * 4;
+  const int64_t vb = (op == ASH_OP_INSERT) ? n * s->value_bytes : 0;
+  r->off_keys = 0;
+  r->off_vals = align256(kb);
+  r->off_idx = r->off_vals + align256(vb);
+  r->off_mask = r->off_idx + align256(n * 4);
+  r->bytes = r->off_mask + align256(n);
+  r->host = s->pinned.take(r->bytes, &r->host_cls);
+  if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
+  std::memcpy(static_cast<char*>(r->host) + r->off_keys, keys_host, kb);
+  if (vb) std::memcpy(static_cast<char*>(r->host) + r->off_vals, values_host, vb);
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      s->pinned.give(r->host, r->host_cls);
+      return fail(ASH_ERR_INVALID, "server is stopping");
+    }
+    r->id = s->next_id++;
+    *request_id_host = r->id;
+    s->pending.push_back(r.get());
+    s->reqs.emplace(r->id, std::move(r));
+    s->stats.submitted += 1;
+  }
+  s->cv_work.notify_one();
+  return ASH_OK;
+}
+
+ash_status ash_server_wait(ash_server* s, uint64_t request_id, int64_t timeout_ms, double* latency_ms_host) {
+  if (!s) return fail(ASH_ERR_INVALID, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return fail(ASH_ERR_INVALID, "unknown or already collected request id");
+  Request* r = it->second.get();
+  auto ready = [&] { return r->gpu_done; };
+  if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    return fail(ASH_ERR_TIMEOUT, "request not finished within the timeout");
+  std::unique_ptr<Request> owned = std::move(it->second);
+  s->reqs.erase(it);
+  const ash_status werr = s->worker_error;
+  lk.unlock();
+  if (werr != ASH_OK) {
+    s->pinned.give(r->host, r->host_cls);
+    return fail(werr, "the serving worker failed a batch");
+  }
+  if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, static_cast<char*>(r->host) + r->off_idx, r->n * 4);
+  std::memcpy(r->mask_user, static_cast<char*>(r->host) + r->off_mask, r->n);
+  s->pinned.give(r->host, r->host_cls);
+  if (latency_ms_host)
+    *latency_ms_host = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  std::lock_guard<std::mutex> lk2(s->mu);
+  s->stats.completed += 1;
+  return ASH_OK;
+}
+
+ash_status ash_server_stats_get(ash_server* s, ash_server_stats* out_host) {
+  if (!s || !out_host) return fail(ASH_ERR_INVALID, "server and out are required");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out_host = s->stats;
+  return ASH_OK;
+}
+
+ash_status ash_server_map(ash_server* s, int32_t tenant, ash_map** out_host) {
+  if (!s || !out_host || tenant < 0 || tenant >= s->cfg.n_tenants) return fail(ASH_ERR_INVALID, "bad arguments");
+  *out_host = s->maps[tenant];
+  return ASH_OK;
+}
+
+ash_status ash_server_stream(ash_server* s, ash_stream* out_host) {
+  if (!s || !out_host) return fail(ASH_ERR_INVALID, "bad arguments");
+  *out_host = reinterpret_cast<ash_stream>(s->s_comp);
+  return ASH_OK;
+}
+
+ash_status ash_server_destroy(ash_server* s) {
+  if (!s) return ASH_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  DeviceGuard g(s->cfg.device);
+  cudaStreamSynchronize(s->s_comp);
+  cudaStreamSynchronize(s->s_h2d);
+  cudaStreamSynchronize(s->s_d2h);
+  for (auto& kv : s->reqs) s->pinned.give(kv.second->host, kv.second->host_cls);
+  for (ash_map* m : s->maps) ash_destroy(m);
+  ash_batch_destroy(s->batch);
+  cudaStreamDestroy(s->s_comp);
+  cudaStreamDestroy(s->s_h2d);
+  cudaStreamDestroy(s->s_d2h);
+  delete s;
+  return ASH_OK;
+}
+
+}  // extern "C"

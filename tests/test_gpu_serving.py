@@ -1,0 +1,130 @@
+"""Multi-tenant serving with continuous batching: every request's result is
+the same when it runs in the mix (many requests in flight, batched across
+tenants) as when its tenant's requests run alone, one plain call at a time;
+and the tenant maps match the oracle.  Bar: bit-exact masks, stored keys and
+value bytes (indices compared through the keys they hold)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import assert_same_map
+from paper_2110_00511_gb300 import ash
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"insert": ash.ASH_OP_INSERT, "find": ash.ASH_OP_FIND, "erase": ash.ASH_OP_ERASE}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2110_00511_gb300 import build
+    build.build()
+    ash.lib()
+
+
+def _trace(seed, n_req, n_tenants, size_range=(200, 30_000), span=60):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for r in range(n_req):
+        op = rng.choice(["insert", "find", "erase"], p=[0.4, 0.45, 0.15])
+        n = int(np.exp(rng.uniform(np.log(size_range[0]), np.log(size_range[1]))))
+        keys = rng.integers(-span, span, size=(n, 3)).astype(np.int32)
+        vals = rng.random(n, dtype=np.float32) if op == "insert" else None
+        reqs.append((int(rng.integers(0, n_tenants)), op, keys, vals))
+    return reqs
+
+
+def _run_alone(reqs, n_tenants, cap):
+    """Each tenant's requests, in order, through plain calls on its own map."""
+    maps = [ash.HashMap(3, cap, [(1,)], [torch.float32]) for _ in range(n_tenants)]
+    out = []
+    for t, op, keys, vals in reqs:
+        k = torch.from_numpy(keys).cuda()
+        if op == "insert":
+            i, m = maps[t].insert(k, [torch.from_numpy(vals).cuda()])
+        elif op == "find":
+            i, m = maps[t].find(k)
+        else:
+            i, m = None, maps[t].erase(k)
+        out.append((None if i is None else i.cpu().numpy(), m.cpu().numpy()))
+    return maps, out
+
+
+def _check_same(reqs, served, alone, server_maps, alone_maps):
+    # an index stays bound to its key until a later erase on that tenant frees it
+    last_erase = {}
+    for j, (t, op, _, _) in enumerate(reqs):
+        if op == "erase":
+            last_erase[t] = j
+    for j, ((t, op, keys, vals), (si, sm), (ai, am)) in enumerate(zip(reqs, served, alone)):
+        assert np.array_equal(sm, am), f"request {j} ({op} on tenant {t}) differs from running alone"
+        if op != "erase" and sm.any() and last_erase.get(t, -1) < j:
+            kb_s = server_maps[t].key_buffer().cpu().numpy()
+            assert np.array_equal(kb_s[si[sm]], keys[sm]), f"request {j}: served index holds another key"
+            assert (si[~sm] == -1).all()
+
+
+def test_served_results_equal_alone_and_oracle():
+    n_t = 4
+    reqs = _trace(1, 80, n_t)
+    srv = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=2048, value_row_bytes=4,
+                     staging_bytes=64 << 20, max_load=0.7, max_batch_requests=256)
+    ids = [srv.submit(t, OPS[op], keys, vals) for t, op, keys, vals in reqs]  # all in flight
+    served = []
+    for rid in ids:
+        i, m, lat = srv.wait(rid)
+        assert lat >= 0.0
+        served.append((i, m))
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["batches"] < len(reqs), st  # batched across tenants
+    assert st["rehashes"] > 0, st  # grew past max_load
+    server_maps = [ash.HashMap.wrap(srv.map_handle(t), 3, [(1,)], [torch.float32]) for t in range(n_t)]
+    alone_maps, alone = _run_alone(reqs, n_t, 2048)
+    _check_same(reqs, served, alone, server_maps, alone_maps)
+    oras = [oracle.OracleMap(3, 2048, [4]) for _ in range(n_t)]
+    for t, op, keys, vals in reqs:
+        if op == "insert":
+            oras[t].insert(keys, [vals])
+        elif op == "erase":
+            oras[t].erase(keys)
+    for t in range(n_t):
+        sk, _ = server_maps[t], None
+        # capacities differ (the server grows at max_load 0.7), the dictionaries do not
+        ok = oracle_state_equal(server_maps[t], oras[t])
+        assert ok, f"tenant {t} map differs from the oracle"
+    srv.close()
+
+
+def oracle_state_equal(hm, om):
+    from parity import gpu_state, oracle_state
+    gk, gv = gpu_state(hm)
+    ok, ov = oracle_state(om)
+    return np.array_equal(gk, ok) and all(np.array_equal(a, b) for a, b in zip(gv, ov))
+
+
+def test_admission_under_a_small_budget():
+    n_t = 3
+    reqs = _trace(2, 30, n_t, size_range=(1000, 200_000), span=200)
+    srv = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=1 << 16, value_row_bytes=4,
+                     staging_bytes=1 << 20, max_load=0.7, max_batch_requests=2)
+    ids = [srv.submit(t, OPS[op], keys, vals) for t, op, keys, vals in reqs]
+    served = [srv.wait(rid)[:2] for rid in ids]
+    server_maps = [ash.HashMap.wrap(srv.map_handle(t), 3, [(1,)], [torch.float32]) for t in range(n_t)]
+    alone_maps, alone = _run_alone(reqs, n_t, 1 << 16)
+    _check_same(reqs, served, alone, server_maps, alone_maps)
+    srv.close()
+
+
+def test_server_rejects_bad_requests():
+    srv = ash.Server(n_tenants=2, key_dim=3, initial_capacity=1024, value_row_bytes=0)
+    with pytest.raises(ash.AshError):
+        srv.submit(5, ash.ASH_OP_FIND, np.zeros((4, 3), np.int32))
+    with pytest.raises(ash.AshError):
+        srv.submit(0, 9, np.zeros((4, 3), np.int32))
+    rid = srv.submit(1, ash.ASH_OP_ACTIVATE, np.arange(12, dtype=np.int32).reshape(4, 3))
+    i, m, _ = srv.wait(rid)
+    assert m.all()
+    with pytest.raises(ash.AshError):
+        srv.wait(rid)  # already collected
+    srv.close()
