@@ -49,6 +49,9 @@ def parse_args(argv=None):
     p.add_argument("--lean", action="store_true", help="timed steps only (no probe, e2e, per-op or cpu legs)")
     p.add_argument("--no-batched", action="store_true", help="skip the many-map batched comparison")
     p.add_argument("--batched-maps", type=int, default=64)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving latency figures")
+    p.add_argument("--serving-rates", type=str, default="2000,5000,10000,20000,50000")
+    p.add_argument("--serving-requests", type=int, default=300)
     return p.parse_args(argv)
 
 
@@ -453,6 +456,10 @@ def main(argv=None):
     if not args.no_batched and not args.lean:
         batched = batched_figures(args, device)
 
+    serving = None
+    if not args.no_serving and not args.lean:
+        serving = serving_figures(args, device)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.lean:
         cpu = cpu_baseline(args, pts_np)
@@ -469,7 +476,7 @@ def main(argv=None):
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "kernels": kernels, "random_read_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "batched": batched, "source_digest": source_digest()}
+                "ops": ops, "batched": batched, "serving": serving, "source_digest": source_digest()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -635,6 +642,123 @@ def batched_figures(args, device, reps=15):
     res["timing"] = ("CUDA events on the stream around the whole service of all maps' batches (the plain "
                      "form's span includes GPU idle time while the host issues its calls)")
     return res
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+
+def serving_figures(args, device, n_tenants=16, clients=8):
+    """Poisson arrivals over 16 resident tenant maps (int32x3 keys, one f32
+    value), request sizes log-uniform in 1e3..1e6 keys, ops 30/60/10
+    insert/find/erase.  Served form: the native continuous-batching server,
+    `clients` threads submitting at their scheduled arrival times.  Baseline:
+    the same requests as sequential plain calls (upload, op, download) in
+    arrival order.  Latency = outputs on the host - scheduled arrival."""
+    import threading
+    import torch
+    from paper_2110_00511_gb300 import ash
+    rng = np.random.default_rng(5)
+    pool_n = 8_000_000
+    key_pool = rng.integers(-(1 << 18), 1 << 18, size=(pool_n, 3)).astype(np.int32)
+    val_pool = rng.random(pool_n, dtype=np.float32)
+    ops_of = np.array([ash.ASH_OP_INSERT, ash.ASH_OP_FIND, ash.ASH_OP_ERASE])
+    rates = [float(x) for x in args.serving_rates.split(",") if x]
+    R = args.serving_requests
+    out = {"tenants": n_tenants, "requests_per_rate": R, "client_threads": clients, "rates": {}}
+
+    def make_trace(rate, seed):
+        g = np.random.default_rng(seed)
+        arr = np.cumsum(g.exponential(1.0 / rate, size=R))
+        sizes = np.exp(g.uniform(np.log(1e3), np.log(1e6), size=R)).astype(np.int64)
+        ops = ops_of[g.choice(3, size=R, p=[0.3, 0.6, 0.1])]
+        tenants = g.integers(0, n_tenants, size=R)
+        starts = g.integers(0, pool_n - sizes)
+        return arr, sizes, ops, tenants, starts
+
+    def summarize(lat_ms, keys_total, span_s):
+        return {"p50_ms": _pct(lat_ms, 0.50), "p99_ms": _pct(lat_ms, 0.99), "p999_ms": _pct(lat_ms, 0.999),
+                "req_per_s": len(lat_ms) / span_s, "keys_per_s": keys_total / span_s}
+
+    srv = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
+                     device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256)
+    maps = [ash.HashMap(3, 1 << 20, [(1,)], [torch.float32], device=device) for _ in range(n_tenants)]
+
+    def run_served(arr, sizes, ops, tenants, starts):
+        lat = [0.0] * len(arr)
+        rids = [None] * len(arr)
+        t0 = time.perf_counter() + 0.02
+
+        def client(c):
+            for r in range(c, len(arr), clients):
+                now = time.perf_counter()
+                if t0 + arr[r] > now:
+                    time.sleep(t0 + arr[r] - now)
+                lo, n = int(starts[r]), int(sizes[r])
+                vals = val_pool[lo:lo + n] if ops[r] == ash.ASH_OP_INSERT else None
+                rids[r] = (srv.submit(int(tenants[r]), int(ops[r]), key_pool[lo:lo + n], vals), time.perf_counter())
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
+        for t in th:
+            t.start()
+        done_at = [0.0] * len(arr)
+        for r in range(len(arr)):
+            while rids[r] is None:
+                time.sleep(0.0002)
+            rid, t_sub = rids[r]
+            _, _, server_ms = srv.wait(rid)
+            lat[r] = (t_sub - (t0 + arr[r])) * 1000.0 + server_ms   # client lag + submit-to-result
+            done_at[r] = t_sub + server_ms / 1000.0
+        for t in th:
+            t.join()
+        return lat, max(done_at) - t0
+
+    def run_sequential(arr, sizes, ops, tenants, starts):
+        lat = []
+        t0 = time.perf_counter() + 0.02
+        t_end = t0
+        for r in range(len(arr)):
+            now = time.perf_counter()
+            if t0 + arr[r] > now:
+                time.sleep(t0 + arr[r] - now)
+            lo, n = int(starts[r]), int(sizes[r])
+            k = torch.from_numpy(key_pool[lo:lo + n]).to(device)
+            hm = maps[int(tenants[r])]
+            if ops[r] == ash.ASH_OP_INSERT:
+                i, m = hm.insert(k, [torch.from_numpy(val_pool[lo:lo + n]).to(device)])
+            elif ops[r] == ash.ASH_OP_FIND:
+                i, m = hm.find(k)
+            else:
+                i, m = None, hm.erase(k)
+            m.cpu().numpy()
+            if i is not None:
+                i.cpu().numpy()
+            t_end = time.perf_counter()
+            lat.append((t_end - (t0 + arr[r])) * 1000.0)
+        return lat, t_end - t0
+
+    # warm both forms (pinned staging classes, device pools, first growth) untimed
+    warm = make_trace(1000.0, 99)
+    run_served(*warm)
+    run_sequential(*warm)
+    for ri, rate in enumerate(rates):
+        trace = make_trace(rate, 100 + ri)
+        keys_total = int(trace[1].sum())
+        st0 = srv.stats()
+        lat, span = run_served(*trace)
+        st1 = srv.stats()
+        served = summarize(lat, keys_total, span)
+        nb = st1["batches"] - st0["batches"]
+        served["avg_requests_per_batch"] = (st1["batched_requests"] - st0["batched_requests"]) / max(1, nb)
+        served["growth_rehashes"] = st1["rehashes"] - st0["rehashes"]
+        seq_lat, seq_span = run_sequential(*trace)
+        seq = summarize(seq_lat, keys_total, seq_span)
+        out["rates"][str(int(rate))] = {"served": served, "sequential_plain": seq,
+                                        "offered_keys_per_s": keys_total / float(trace[0][-1])}
+    srv.close()
+    del maps
+    return out
 
 
 if __name__ == "__main__":

@@ -186,6 +186,12 @@ ash_status ash_rehash(ash_map* map, int64_t new_capacity, ash_stream stream);
 /* Grows the capacity to at least new_capacity (no-op if already there). */
 ash_status ash_reserve(ash_map* map, int64_t new_capacity, ash_stream stream);
 
+/* Like ash_reserve, but enqueued on the stream with no host synchronisation:
+ * the live count stays on the device (the listing writes it, the rebuild
+ * reads it).  Keeps buffer indices.  Pointers from ash_key_buffer /
+ * ash_value_buffer are invalidated. */
+ash_status ash_reserve_async(ash_map* map, int64_t new_capacity, ash_stream stream);
+
 /* Removes every entry: empty table, identity heap, t = 0.  Value bytes stay. */
 ash_status ash_clear(ash_map* map, ash_stream stream);
 

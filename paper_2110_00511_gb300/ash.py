@@ -90,6 +90,7 @@ _SIGS = {
     "ash_n_values": (ctypes.c_int, [_P]),
     "ash_rehash": (_I32, [_P, _I64, _P]),
     "ash_reserve": (_I32, [_P, _I64, _P]),
+    "ash_reserve_async": (_I32, [_P, _I64, _P]),
     "ash_clear": (_I32, [_P, _P]),
     "ash_key_buffer": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "ash_value_buffer": (_I32, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
@@ -289,6 +290,10 @@ def ash_rehash(handle, new_capacity=0, stream=None):
 
 def ash_reserve(handle, new_capacity, stream=None):
     _check(lib().ash_reserve(handle, int(new_capacity), stream if stream is not None else _stream()))
+
+
+def ash_reserve_async(handle, new_capacity, stream=None):
+    _check(lib().ash_reserve_async(handle, int(new_capacity), stream if stream is not None else _stream()))
 
 
 def ash_clear(handle, stream=None):
@@ -561,6 +566,9 @@ class HashMap:
 
     def reserve(self, new_capacity):
         ash_reserve(self._h, new_capacity, _stream(self.device))
+
+    def reserve_async(self, new_capacity):
+        ash_reserve_async(self._h, new_capacity, _stream(self.device))
 
     def clear(self):
         ash_clear(self._h, _stream(self.device))

@@ -98,6 +98,18 @@ void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L) {
 
 __global__ void set_top_used_kernel(Ctrl* ctrl, unsigned long long top_used) { ctrl->top_used = top_used; }
 
+// used slots := the listed live count (heap top unchanged), after a rebuild
+// whose count only the device knows.
+__global__ void set_used_from_count_kernel(Ctrl* ctrl) {
+  const unsigned long long top = ctrl->top_used & 0xFFFFFFFFull;
+  ctrl->top_used = (ctrl->count << 32) | top;
+}
+
+void launch_set_used_from_count(Ctrl* ctrl, const Launch& L) {
+  TraceScope ts(kKSetCtrl, L.stream);
+  set_used_from_count_kernel<<<1, 1, 0, L.stream>>>(ctrl);
+}
+
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L) {
   const unsigned long long v = (static_cast<unsigned long long>(used) << 32) | static_cast<unsigned long long>(top);
   TraceScope ts(kKSetCtrl, L.stream);

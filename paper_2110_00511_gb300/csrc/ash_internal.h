@@ -82,6 +82,8 @@ TableView view_of(const ash_map* m);
 ash_status check_keys(const ash_map* m, const void* keys, int64_t n);
 // x2 growth / table rebuild so that a batch of n insert keys fits (may synchronise st).
 ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st);
+// Growth to new_capacity >= capacity, enqueued on st with no host synchronisation.
+ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st);
 
 }  // namespace host
 }  // namespace ash

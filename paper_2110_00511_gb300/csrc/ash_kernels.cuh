@@ -532,9 +532,14 @@ __global__ void __launch_bounds__(256) erase_resolve_kernel(TableView t, int64_t
 // preserve: the entry keeps buffer index list[j]; otherwise it becomes j.
 // The key row is copied to kb_dst when kb_dst != kb_src or !preserve.
 template <int D, int S>
+// n_dev (optional): the live count on the device (written by the listing);
+// the kernel then processes min(n, *n_dev) entries, so a rebuild can be
+// enqueued without the host knowing the count.
 __global__ void __launch_bounds__(256) rebuild_kernel(TableView t, const int32_t* __restrict__ kb_src,
-                                                      const int32_t* __restrict__ list, int64_t n, int preserve,
+                                                      const int32_t* __restrict__ list, int64_t n,
+                                                      const unsigned long long* __restrict__ n_dev, int preserve,
                                                       int copy_keys) {
+  if (n_dev) n = min(n, static_cast<int64_t>(*n_dev));
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride) {
     const uint32_t a = static_cast<uint32_t>(list[j]);
@@ -588,7 +593,8 @@ struct DimKernels {
   void (*commit)(int kpt, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const ValueRow*,
                  const Launch&);
   void (*erase_mark)(int S, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
-  void (*rebuild)(int S, const TableView&, const int32_t*, const int32_t*, int64_t, int, int, const Launch&);
+  void (*rebuild)(int S, const TableView&, const int32_t*, const int32_t*, int64_t, const unsigned long long*, int, int,
+                  const Launch&);
 };
 
 template <int D>
@@ -658,16 +664,16 @@ struct DimLaunchers {
     else erase_mark_s<16>(t, keys, n, slot_out, L);
   }
   template <int S>
-  static void rebuild_s(const TableView& t, const int32_t* kb_src, const int32_t* list, int64_t n, int preserve,
-                        int copy_keys, const Launch& L) {
+  static void rebuild_s(const TableView& t, const int32_t* kb_src, const int32_t* list, int64_t n,
+                        const unsigned long long* n_dev, int preserve, int copy_keys, const Launch& L) {
     TraceScope ts(kKRebuild, L.stream);
-    rebuild_kernel<D, S><<<grid_for(n, L), L.block, 0, L.stream>>>(t, kb_src, list, n, preserve, copy_keys);
+    rebuild_kernel<D, S><<<grid_for(n, L), L.block, 0, L.stream>>>(t, kb_src, list, n, n_dev, preserve, copy_keys);
   }
-  static void rebuild(int S, const TableView& t, const int32_t* kb_src, const int32_t* list, int64_t n, int preserve,
-                      int copy_keys, const Launch& L) {
-    if (S == 4) rebuild_s<4>(t, kb_src, list, n, preserve, copy_keys, L);
-    else if (S == 8) rebuild_s<8>(t, kb_src, list, n, preserve, copy_keys, L);
-    else rebuild_s<16>(t, kb_src, list, n, preserve, copy_keys, L);
+  static void rebuild(int S, const TableView& t, const int32_t* kb_src, const int32_t* list, int64_t n,
+                      const unsigned long long* n_dev, int preserve, int copy_keys, const Launch& L) {
+    if (S == 4) rebuild_s<4>(t, kb_src, list, n, n_dev, preserve, copy_keys, L);
+    else if (S == 8) rebuild_s<8>(t, kb_src, list, n, n_dev, preserve, copy_keys, L);
+    else rebuild_s<16>(t, kb_src, list, n, n_dev, preserve, copy_keys, L);
   }
   static DimKernels table() {
     DimKernels k;

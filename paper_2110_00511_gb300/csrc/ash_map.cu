@@ -368,7 +368,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
   m->heap = heap;
   m->vb = vb;
   ash::TableView tv = view_of(m);
-  m->K.rebuild(m->S, tv, old.kb, list, size, preserve ? 1 : 0, (!preserve) ? 1 : 0, L);
+  m->K.rebuild(m->S, tv, old.kb, list, size, nullptr, preserve ? 1 : 0, (!preserve) ? 1 : 0, L);
   s = check_launch("rehash rebuild");
   if (s != ASH_OK) return s;
   ash::launch_set_top_used(m->ctrl, size, size, L);
@@ -383,6 +383,86 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
   m->size_ub = size;
   m->used_ub = size;
   return check_launch("rehash");
+}
+
+// Grows the capacity to new_capacity (>= capacity) without any host
+// synchronisation: the live count never leaves the device.  The listing
+// writes it to the control block, the rebuild kernel reads it there, and the
+// used-slot count is set from it.  Buffer indices are kept.
+ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
+  if (new_capacity < m->capacity) return fail(ASH_ERR_INVALID, "grow_async cannot shrink");
+  const ash::Launch L = launch_of(m, st);
+  const int64_t c = m->capacity;
+  int32_t* list = static_cast<int32_t*>(dev_alloc(m, c * 4, st));
+  if (!list) return fail(ASH_ERR_OOM, "growth list allocation failed");
+  ash_status s = ensure_list_scratch(m, st);
+  if (s != ASH_OK) {
+    dev_free(m, list, st);
+    return s;
+  }
+  ash::launch_list_active(m->heap, c, m->ctrl, m->list_scratch, list, c, L);
+  const int64_t n_slots = slots_for(new_capacity, m->tuning);
+  if (n_slots >= (int64_t{1} << 31)) {
+    dev_free(m, list, st);
+    return fail(ASH_ERR_INVALID, "capacity too large for 31-bit slot indices");
+  }
+  uint64_t* slots = static_cast<uint64_t*>(dev_alloc(m, n_slots * 8, st));
+  int32_t* kb = m->kb;
+  int32_t* heap = m->heap;
+  std::vector<void*> vb = m->vb;
+  const bool grow = new_capacity != c;
+  bool ok = slots != nullptr;
+  if (grow && ok) {
+    kb = static_cast<int32_t*>(dev_alloc(m, new_capacity * m->ks * 4, st));
+    heap = static_cast<int32_t*>(dev_alloc(m, new_capacity * 4, st));
+    ok = kb && heap;
+    for (int j = 0; j < m->n_values && ok; ++j) {
+      vb[j] = dev_alloc(m, new_capacity * m->row_bytes[j], st);
+      ok = vb[j] != nullptr;
+    }
+  }
+  if (!ok) {
+    dev_free(m, list, st);
+    dev_free(m, slots, st);
+    if (grow) {
+      if (kb != m->kb) dev_free(m, kb, st);
+      if (heap != m->heap) dev_free(m, heap, st);
+      for (int j = 0; j < m->n_values; ++j)
+        if (vb[j] != m->vb[j]) dev_free(m, vb[j], st);
+    }
+    return fail(ASH_ERR_OOM, "growth allocation failed");
+  }
+  ASH_CUDA(cudaMemsetAsync(slots, 0xFF, n_slots * 8, st));
+  if (grow) {
+    ASH_CUDA(cudaMemcpyAsync(kb, m->kb, c * m->ks * 4, cudaMemcpyDeviceToDevice, st));
+    ASH_CUDA(cudaMemcpyAsync(heap, m->heap, c * 4, cudaMemcpyDeviceToDevice, st));
+    ash::launch_iota(heap, c, new_capacity, L);
+    for (int j = 0; j < m->n_values; ++j) {
+      const int64_t rb = m->row_bytes[j];
+      ASH_CUDA(cudaMemcpyAsync(vb[j], m->vb[j], c * rb, cudaMemcpyDeviceToDevice, st));
+      ASH_CUDA(cudaMemsetAsync(static_cast<char*>(vb[j]) + c * rb, 0, (new_capacity - c) * rb, st));
+    }
+  }
+  ash_map old = *m;
+  m->S = m->tuning.slots_per_bucket;
+  m->slots = slots;
+  m->n_slots = n_slots;
+  m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
+  m->capacity = new_capacity;
+  m->kb = kb;
+  m->heap = heap;
+  m->vb = vb;
+  m->K.rebuild(m->S, view_of(m), old.kb, list, c, &m->ctrl->count, 1, 0, L);
+  ash::launch_set_used_from_count(m->ctrl, L);
+  dev_free(m, old.slots, st);
+  if (grow) {
+    dev_free(m, old.kb, st);
+    dev_free(m, old.heap, st);
+    for (void* p : old.vb) dev_free(m, p, st);
+  }
+  dev_free(m, list, st);
+  m->used_ub = m->size_ub;
+  return check_launch("grow_async");
 }
 
 // Makes room for a batch of n insert/activate keys: x2 growth when the live
@@ -658,6 +738,15 @@ ash_status ash_reserve(ash_map* m, int64_t new_capacity, ash_stream stream) {
   if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
   if (new_capacity <= m->capacity) return ASH_OK;
   return ash_rehash(m, new_capacity, stream);
+}
+
+ash_status ash_reserve_async(ash_map* m, int64_t new_capacity, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (new_capacity <= m->capacity) return ASH_OK;
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  return grow_async(m, new_capacity, st);
 }
 
 ash_status ash_clear(ash_map* m, ash_stream stream) {

@@ -27,6 +27,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -98,8 +99,14 @@ struct Request {
   bool delivered = false;
 };
 
+// A launched batch.  It owns copies of what the worker must release after the
+// batch finishes (device staging and its byte count), because once the
+// completion callback publishes the requests as done, ash_server_wait may
+// free them at any time; only the callback touches `reqs`, before that point.
 struct Batch {
   std::vector<Request*> reqs;
+  std::vector<char*> dev;
+  int64_t staged = 0;
   struct ash_server* server = nullptr;
   bool done = false;
 };
@@ -125,6 +132,7 @@ struct ash_server {
   uint64_t next_id = 1;
   bool stop = false;
   ash_status worker_error = ASH_OK;
+  std::string worker_msg;
   std::thread worker;
   ash_server_stats stats{};
 };
@@ -147,21 +155,19 @@ void CUDART_CB on_batch_done(void* arg) {
   s->cv_work.notify_one();
 }
 
-// Worker-side: grow tenant maps so that an insert of n keys keeps the live /
-// capacity ratio at or below max_load (synchronises the compute stream).
+// Worker-side: before an insert of n keys, grow the tenant map (x2 until it
+// fits) when the host's upper bound on its live entries would pass max_load
+// of the capacity.  The growth runs on the device, in stream order, with no
+// host synchronisation (grow_async), so it does not stall the pipeline.
 ash_status grow_for_insert(ash_server* s, ash_map* m, int64_t n) {
   const double lim = s->cfg.max_load;
-  if (static_cast<double>(m->size_ub + n) <= lim * static_cast<double>(m->capacity)) return ASH_OK;
-  int64_t size = 0;
-  ash_status st = ash_size(m, &size, reinterpret_cast<ash_stream>(s->s_comp));
-  if (st != ASH_OK) return st;
+  const double need = static_cast<double>(m->size_ub + n);
+  if (need <= lim * static_cast<double>(m->capacity)) return ASH_OK;
   int64_t c = m->capacity;
-  while (static_cast<double>(size + n) > lim * static_cast<double>(c)) c *= 2;
-  if (c != m->capacity) {
-    st = ash_reserve(m, c, reinterpret_cast<ash_stream>(s->s_comp));
-    if (st != ASH_OK) return st;
-    s->stats.rehashes += 1;
-  }
+  while (need > lim * static_cast<double>(c)) c *= 2;
+  ash_status st = grow_async(m, c, s->s_comp);
+  if (st != ASH_OK) return st;
+  s->stats.rehashes += 1;
   return ASH_OK;
 }
 
@@ -173,11 +179,8 @@ void worker_loop(ash_server* s) {
     while (!s->inflight.empty() && s->inflight.front()->done) {
       Batch* b = s->inflight.front();
       s->inflight.pop_front();
-      for (Request* r : b->reqs) {
-        cudaFreeAsync(r->dev, s->s_d2h);
-        r->dev = nullptr;
-        s->staged_bytes -= r->bytes;
-      }
+      for (char* p : b->dev) cudaFreeAsync(p, s->s_d2h);
+      s->staged_bytes -= b->staged;
       delete b;
     }
     if (s->stop && s->pending.empty() && s->admitted.empty() && s->inflight.empty()) break;
@@ -240,35 +243,50 @@ void worker_loop(ash_server* s) {
       }
     }
     if (st == ASH_OK) {
-      cudaEvent_t up, comp;
+      cudaEvent_t up = nullptr, comp = nullptr;
       cudaEventCreateWithFlags(&up, cudaEventDisableTiming);
       cudaEventCreateWithFlags(&comp, cudaEventDisableTiming);
       cudaEventRecord(up, s->s_h2d);
       cudaStreamWaitEvent(s->s_comp, up, 0);
       st = ash_batch_run(s->batch, ops.data(), static_cast<int>(ops.size()), reinterpret_cast<ash_stream>(s->s_comp));
-      cudaEventRecord(comp, s->s_comp);
-      cudaStreamWaitEvent(s->s_d2h, comp, 0);
-      for (Request* r : pick) {
-        const int64_t out_bytes = r->bytes - r->off_idx;
-        cudaMemcpyAsync(static_cast<char*>(r->host) + r->off_idx, r->dev + r->off_idx, out_bytes,
-                        cudaMemcpyDeviceToHost, s->s_d2h);
+      if (st == ASH_OK) {
+        cudaEventRecord(comp, s->s_comp);
+        cudaStreamWaitEvent(s->s_d2h, comp, 0);
+        for (Request* r : pick) {
+          const int64_t out_bytes = r->bytes - r->off_idx;
+          cudaMemcpyAsync(static_cast<char*>(r->host) + r->off_idx, r->dev + r->off_idx, out_bytes,
+                          cudaMemcpyDeviceToHost, s->s_d2h);
+        }
       }
       cudaEventDestroy(up);
       cudaEventDestroy(comp);
-      Batch* b = new Batch();
-      b->reqs = pick;
-      b->server = s;
-      lk.lock();
-      s->inflight.push_back(b);
-      s->stats.batches += 1;
-      s->stats.batched_requests += static_cast<int64_t>(pick.size());
-      lk.unlock();
-      if (cudaLaunchHostFunc(s->s_d2h, on_batch_done, b) != cudaSuccess) st = ASH_ERR_CUDA;
+      if (st == ASH_OK) {
+        Batch* b = new Batch();
+        b->reqs = pick;
+        for (Request* r : pick) {
+          b->dev.push_back(r->dev);
+          b->staged += r->bytes;
+        }
+        b->server = s;
+        lk.lock();
+        s->inflight.push_back(b);
+        s->stats.batches += 1;
+        s->stats.batched_requests += static_cast<int64_t>(pick.size());
+        lk.unlock();
+        if (cudaLaunchHostFunc(s->s_d2h, on_batch_done, b) != cudaSuccess) {
+          st = cuda_fail(cudaGetLastError(), "cudaLaunchHostFunc");
+          lk.lock();
+          s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), b));
+          lk.unlock();
+          delete b;
+        }
+      }
     }
     lk.lock();
     if (st != ASH_OK) {
       // fail the picked requests so no waiter hangs, and give back their staging
       s->worker_error = st;
+      s->worker_msg = ash_last_error();
       for (Request* r : pick) {
         if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
         r->dev = nullptr;
@@ -394,10 +412,11 @@ ash_status ash_server_wait(ash_server* s, uint64_t request_id, int64_t timeout_m
   std::unique_ptr<Request> owned = std::move(it->second);
   s->reqs.erase(it);
   const ash_status werr = s->worker_error;
+  const std::string wmsg = s->worker_msg;
   lk.unlock();
   if (werr != ASH_OK) {
     s->pinned.give(r->host, r->host_cls);
-    return fail(werr, "the serving worker failed a batch");
+    return fail(werr, "the serving worker failed a batch: " + wmsg);
   }
   if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, static_cast<char*>(r->host) + r->off_idx, r->n * 4);
   std::memcpy(r->mask_user, static_cast<char*>(r->host) + r->off_mask, r->n);

@@ -178,6 +178,35 @@ def test_rehash_preserves_indices_and_compacts():
     assert_same_map(hm, om)
 
 
+def test_reserve_async_keeps_map_and_indices():
+    """Growth with no host synchronisation (the live count stays on the
+    device) keeps every key, value and buffer index; later ops still match."""
+    rng = np.random.default_rng(21)
+    keys = rng.integers(-300, 300, size=(40_000, 3)).astype(np.int32)
+    vals = rng.random(40_000, dtype=np.float32)
+    hm = ash.HashMap(3, 50_000, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, 50_000, [4])
+    hm.insert(dev(keys), [dev(vals)])
+    om.insert(keys, [vals])
+    hm.erase(dev(keys[:7000]))
+    om.erase(keys[:7000])
+    q = dev(keys)
+    bi, bm = hm.find(q)
+    hm.reserve_async(200_000)
+    ai, am = hm.find(q)  # same stream, after the growth
+    assert torch.equal(bi, ai) and torch.equal(bm, am)
+    assert hm.capacity() == 200_000
+    om.rehash(200_000)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+    more = rng.integers(300, 400, size=(30_000, 3)).astype(np.int32)
+    mv = rng.random(30_000, dtype=np.float32)
+    gi, gm = hm.insert(dev(more), [dev(mv)])
+    oi, omask = om.insert(more, [mv])
+    assert_op_parity(hm, more, gi, gm, oi, omask)
+    assert_same_map(hm, om)
+
+
 def test_clear_and_reuse():
     rng = np.random.default_rng(9)
     keys = rng.integers(-50, 50, size=(20_000, 2)).astype(np.int32)
