@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(kListThreads) compact_live_kernel(const uint32
                                                                     int32_t* __restrict__ out, int64_t out_cap) {
   __shared__ int s_warp[33];
   __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31;
   const int64_t wi = static_cast<int64_t>(blockIdx.x) * kListThreads + threadIdx.x;
   uint32_t live = ~words[wi];
   const int64_t lo = wi * 32;
@@ -55,12 +56,17 @@ __global__ void __launch_bounds__(kListThreads) compact_live_kernel(const uint32
   const int off = block_exclusive_scan(__popc(live), total, s_warp);
   if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctrl->count, static_cast<unsigned long long>(total)) : 0ull;
   __syncthreads();
-  int64_t o = static_cast<int64_t>(s_base) + off;
-  while (live) {
-    const int b = __ffs(live) - 1;
-    live &= live - 1u;
-    if (o < out_cap) out[o] = static_cast<int32_t>(lo + b);
-    ++o;
+  const int64_t base = static_cast<int64_t>(s_base);
+  const int64_t w0 = wi - lane;  // first word of this warp
+  // the warp writes its 32 words one after another, one bit per lane, so each
+  // store instruction covers a contiguous run of the output
+  for (int w = 0; w < 32; ++w) {
+    const uint32_t word = __shfl_sync(0xFFFFFFFFu, live, w);
+    const int o = __shfl_sync(0xFFFFFFFFu, off, w);
+    if ((word >> lane) & 1u) {
+      const int64_t dst = base + o + __popc(word & ((1u << lane) - 1u));
+      if (dst < out_cap) out[dst] = static_cast<int32_t>((w0 + w) * 32 + lane);
+    }
   }
 }
 
