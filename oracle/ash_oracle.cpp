@@ -22,7 +22,7 @@
 //     insert them into the enlarged buffers;
 //   * the voxel quantisation of Sec. 6.1 / Eq. (11): floor(p / s) in float32.
 //
-// Readings of points the paper leaves open (each listed in the design doc):
+// Readings of points the paper leaves open:
 //   * within one batch, the FIRST occurrence (lowest input position) of a key
 //     wins; later duplicates get mask 0;
 //   * the index returned with mask 0 is -1 (the paper says "undefined");
