@@ -210,6 +210,19 @@ ash_status ash_heap_buffer(ash_map* map, int32_t** heap_host, int32_t** top_host
 ash_status ash_gather_keys(ash_map* map, const int32_t* indices, int64_t n, int32_t* out,
                            ash_stream stream);
 
+/* Gathers value rows: out row r = vB_j(indices[r]) (row_bytes of buffer j
+ * each); rows whose index is outside [0, c) are written as zeros. */
+ash_status ash_gather_values(ash_map* map, int j, const int32_t* indices, int64_t n, void* out, ash_stream stream);
+
+/* Radius neighbour query (the radius search of Sec. 6.2): for every key
+ * keys[r] and every integer offset o in [-radius, radius]^key_dim, enumerated
+ * row-major (the first coordinate slowest), finds keys[r] + o (int32
+ * wrap-around).  buf_indices and masks are [n, (2*radius+1)^key_dim]; entry
+ * [r, m] is the masked query (Eq. (4)) of keys[r] + offset m.  The offset
+ * keys are formed inside the kernel, never materialised.  radius <= 8. */
+ash_status ash_find_neighbors(ash_map* map, const int32_t* keys, int64_t n, int32_t radius, int32_t* buf_indices,
+                              uint8_t* masks, ash_stream stream);
+
 ash_status ash_get_tuning(const ash_map* map, ash_tuning* out_host);
 ash_status ash_set_tuning(ash_map* map, const ash_tuning* tuning_host);
 

@@ -96,6 +96,8 @@ _SIGS = {
     "ash_value_buffer": (_I32, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "ash_heap_buffer": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "ash_gather_keys": (_I32, [_P, _P, _I64, _P, _P]),
+    "ash_gather_values": (_I32, [_P, ctypes.c_int, _P, _I64, _P, _P]),
+    "ash_find_neighbors": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "ash_get_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_sync_status": (_I32, [_P, _P]),
@@ -580,6 +582,44 @@ class HashMap:
         out = torch.empty((indices.numel(), self.key_dim), dtype=torch.int32, device=self.device)
         ash_gather_keys(self._h, indices.to(torch.int32).contiguous(), out)
         return out
+
+    def gather_values(self, indices, j=0):
+        """[n, *shape_j] rows of value buffer j at `indices` (zeros outside [0, c))."""
+        idx = indices.to(torch.int32).contiguous()
+        out = torch.empty((idx.numel(), *self.value_shapes[j]), dtype=self.value_dtypes[j], device=self.device)
+        _check(lib().ash_gather_values(self._h, j, _ptr(idx), idx.numel(), _ptr(out), _stream(self.device)))
+        return out
+
+    def find_neighbors(self, keys, radius=1):
+        """Masked queries of keys[r] + every offset in [-radius, radius]^d:
+        (buf_indices, masks), each [n, (2*radius+1)^d]."""
+        keys = self._keys(keys)
+        k = (2 * radius + 1) ** self.key_dim
+        idx = torch.empty((keys.shape[0], k), dtype=torch.int32, device=self.device)
+        mask = torch.empty((keys.shape[0], k), dtype=torch.bool, device=self.device)
+        _check(lib().ash_find_neighbors(self._h, _ptr(keys), keys.shape[0], int(radius), _ptr(idx), _ptr(mask),
+                                        _stream(self.device)))
+        return idx, mask
+
+    def export(self):
+        """Checkpoint of the live entries: {"keys": [n, d], "values": [..],
+        "capacity": c} (device tensors; save with torch.save)."""
+        act = self.active_indices()
+        return {"keys": self.gather_keys(act), "values": [self.gather_values(act, j) for j in range(len(self.value_shapes))],
+                "capacity": self.capacity(), "key_dim": self.key_dim,
+                "value_shapes": self.value_shapes, "value_dtypes": [str(d) for d in self.value_dtypes]}
+
+    @classmethod
+    def from_export(cls, state, device=None, tuning=None):
+        """Re-creates a map from export(): a bulk insert of the saved entries."""
+        dts = [getattr(torch, d.replace("torch.", "")) for d in state["value_dtypes"]]
+        hm = cls(state["key_dim"], state["capacity"], state["value_shapes"], dts, device=device, tuning=tuning)
+        keys = state["keys"].to(hm.device).contiguous()
+        if len(dts):
+            hm.insert(keys, [v.to(hm.device).contiguous() for v in state["values"]])
+        else:
+            hm.activate(keys)
+        return hm
 
     def key_buffer(self):
         """int32 [capacity, key_dim] view of kB (valid until the next rehash)."""

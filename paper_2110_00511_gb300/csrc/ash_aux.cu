@@ -200,6 +200,34 @@ void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, cons
   gather_keys_kernel<<<grid_for(n, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, out);
 }
 
+// Warp per output row: out row r <- value buffer row indices[r] (zeros for
+// indices outside [0, capacity)).
+__global__ void __launch_bounds__(256) gather_values_kernel(const char* __restrict__ src, int64_t row_bytes, int vec,
+                                                            int64_t capacity, const int32_t* __restrict__ indices,
+                                                            int64_t n, char* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const int32_t i = indices[r];
+    char* dst = out + r * row_bytes;
+    if (i >= 0 && i < capacity) {
+      copy_row(dst, src + static_cast<int64_t>(i) * row_bytes, row_bytes, vec, lane, 32);
+    } else {
+      for (int64_t b = lane; b < row_bytes; b += 32) dst[b] = 0;
+    }
+  }
+}
+
+void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t capacity, const int32_t* indices,
+                          int64_t n, void* out, const Launch& L) {
+  if (n == 0) return;
+  TraceScope ts(kKGatherValues, L.stream);
+  int64_t g = (n * 32 + L.block - 1) / L.block;
+  if (g > L.grid_cap) g = L.grid_cap;
+  gather_values_kernel<<<static_cast<int>(g < 1 ? 1 : g), L.block, 0, L.stream>>>(
+      static_cast<const char*>(src), row_bytes, vec, capacity, indices, n, static_cast<char*>(out));
+}
+
 // ------------------------------------------------------------- quantisation
 // floor(p / cell) in float32 with IEEE division (this file is compiled without
 // fast-math), then float -> int32 conversion rounding toward minus infinity

@@ -37,11 +37,9 @@
 namespace ash {
 
 // ---------------------------------------------------------------------- find
-// Scalar lookup of input row pos from its home bucket (the slow path of find).
+// Scalar lookup of key k from its home bucket.
 template <int D, int S>
-__device__ __noinline__ int32_t find_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
-  int32_t k[D];
-  load_input_key<D>(keys, pos, k);
+__device__ __forceinline__ int32_t find_key(const TableView& t, const int32_t (&k)[D]) {
   const uint64_t h = hash_key<D>(k);
   const uint32_t fp = fingerprint(h);
   uint32_t b = home_bucket(h, t.n_buckets);
@@ -61,6 +59,42 @@ __device__ __noinline__ int32_t find_one(const TableView t, const int32_t* __res
     b = next_bucket(b, t.n_buckets);
   }
   return -1;
+}
+
+// Scalar lookup of input row pos (the slow path of find).
+template <int D, int S>
+__device__ __noinline__ int32_t find_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
+  int32_t k[D];
+  load_input_key<D>(keys, pos, k);
+  return find_key<D, S>(t, k);
+}
+
+// Radius neighbour query (the radius search of Sec. 6.2): thread per (query,
+// offset) pair.  Offsets enumerate [-radius, radius]^D row-major (the last
+// coordinate fastest) and are added with int32 wrap-around; the (2r+1)^D
+// query keys are never materialised.  Outputs are [n, (2r+1)^D].
+template <int D, int S>
+__global__ void __launch_bounds__(256) neighbors_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+                                                        int radius, int64_t n_off, int32_t* __restrict__ idx,
+                                                        uint8_t* __restrict__ mask) {
+  const int64_t total = n * n_off;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int width = 2 * radius + 1;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t r = e / n_off;
+    int64_t o = e - r * n_off;
+    int32_t k[D];
+    load_input_key<D>(keys, r, k);
+#pragma unroll
+    for (int j = D - 1; j >= 0; --j) {
+      const int digit = static_cast<int>(o % width);
+      o /= width;
+      k[j] = static_cast<int32_t>(static_cast<uint32_t>(k[j]) + static_cast<uint32_t>(digit - radius));
+    }
+    const int32_t out = find_key<D, S>(t, k);
+    idx[e] = out;
+    mask[e] = out >= 0 ? 1 : 0;
+  }
 }
 
 // KPT keys per thread: positions base, base + blockDim.x, ... so every load
@@ -595,6 +629,7 @@ struct DimKernels {
   void (*erase_mark)(int S, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
   void (*rebuild)(int S, const TableView&, const int32_t*, const int32_t*, int64_t, const unsigned long long*, int, int,
                   const Launch&);
+  void (*neighbors)(int S, const TableView&, const int32_t*, int64_t, int, int64_t, int32_t*, uint8_t*, const Launch&);
 };
 
 template <int D>
@@ -675,8 +710,21 @@ struct DimLaunchers {
     else if (S == 8) rebuild_s<8>(t, kb_src, list, n, n_dev, preserve, copy_keys, L);
     else rebuild_s<16>(t, kb_src, list, n, n_dev, preserve, copy_keys, L);
   }
+  template <int S>
+  static void neighbors_s(const TableView& t, const int32_t* keys, int64_t n, int radius, int64_t n_off, int32_t* idx,
+                          uint8_t* mask, const Launch& L) {
+    TraceScope ts(kKNeighbors, L.stream);
+    neighbors_kernel<D, S><<<grid_for(n * n_off, L), L.block, 0, L.stream>>>(t, keys, n, radius, n_off, idx, mask);
+  }
+  static void neighbors(int S, const TableView& t, const int32_t* keys, int64_t n, int radius, int64_t n_off,
+                        int32_t* idx, uint8_t* mask, const Launch& L) {
+    if (S == 4) neighbors_s<4>(t, keys, n, radius, n_off, idx, mask, L);
+    else if (S == 8) neighbors_s<8>(t, keys, n, radius, n_off, idx, mask, L);
+    else neighbors_s<16>(t, keys, n, radius, n_off, idx, mask, L);
+  }
   static DimKernels table() {
     DimKernels k;
+    k.neighbors = &neighbors;
     k.find = &find;
     k.claim = &claim;
     k.commit = &commit;

@@ -796,6 +796,37 @@ ash_status ash_gather_keys(ash_map* m, const int32_t* indices, int64_t n, int32_
   return check_launch("gather_keys");
 }
 
+ash_status ash_gather_values(ash_map* m, int j, const int32_t* indices, int64_t n, void* out, ash_stream stream) {
+  if (!m) return fail(ASH_ERR_INVALID, "map is NULL");
+  if (j < 0 || j >= m->n_values) return fail(ASH_ERR_INVALID, "value buffer index out of range");
+  if (n < 0) return fail(ASH_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return ASH_OK;
+  if (!indices || !out) return fail(ASH_ERR_INVALID, "indices and out are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t rb = m->row_bytes[j];
+  ash::launch_gather_values(m->vb[j], rb, vec_width(rb, m->vb[j], out), m->capacity, indices, n, out, launch_of(m, st));
+  return check_launch("gather_values");
+}
+
+ash_status ash_find_neighbors(ash_map* m, const int32_t* keys, int64_t n, int32_t radius, int32_t* buf_indices,
+                              uint8_t* masks, ash_stream stream) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (radius < 0 || radius > 8) return fail(ASH_ERR_INVALID, "radius must be in 0..8");
+  int64_t n_off = 1;
+  for (int j = 0; j < m->key_dim; ++j) n_off *= 2 * radius + 1;
+  if (n_off > (int64_t{1} << 20) || n * n_off >= (int64_t{1} << 40))
+    return fail(ASH_ERR_INVALID, "too many neighbour queries");
+  if (n == 0) return ASH_OK;
+  if (!buf_indices || !masks) return fail(ASH_ERR_INVALID, "buf_indices and masks are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  m->K.neighbors(m->S, view_of(m), keys, n, radius, n_off, buf_indices, masks, launch_of(m, st));
+  return check_launch("find_neighbors");
+}
+
 ash_status ash_get_tuning(const ash_map* m, ash_tuning* out_host) {
   if (!m || !out_host) return fail(ASH_ERR_INVALID, "map and out are required");
   *out_host = m->tuning;

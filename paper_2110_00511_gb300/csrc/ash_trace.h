@@ -22,6 +22,8 @@ enum KernelKind {
   kKSetCtrl,
   kKBatch,
   kKSynthKeys,
+  kKNeighbors,
+  kKGatherValues,
   kKernelKinds
 };
 

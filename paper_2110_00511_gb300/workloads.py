@@ -138,13 +138,16 @@ def _rotation(yaw: float, pitch: float) -> np.ndarray:
 
 
 def tsdf_block_frames(n_frames: int = 200, seed: int = 0, voxel: float = 0.006, block: int = 8,
-                      cam: Camera | None = None, stride: int = 1):
+                      cam: Camera | None = None, stride: int = 1, orbit: float = 0.4, turn: float = 0.25,
+                      drift: float = 0.01):
     """Yields int32 [H*W/stride^2, 3] voxel-block keys, one array per frame.
 
     Depth per frame is a smooth random field (a sum of 8 low-frequency
-    sinusoids) mapped into [0.5, 4] m; the camera moves on a slow seeded
-    trajectory inside a 10 m room so blocks are revisited.  Block edge is
-    voxel * block (48 mm for the 6 mm / 8^3 setting of Sec. 6.2)."""
+    sinusoids, phases drifting by `drift` rad per frame) mapped into
+    [0.5, 4] m.  The camera moves slowly inside a 10 m room (an orbit of
+    `orbit` m while turning through `turn` of a full revolution), so blocks are
+    revisited.  Block edge is voxel * block (48 mm for the 6 mm / 8^3 setting
+    of Sec. 6.2)."""
     cam = cam or Camera()
     rng = np.random.default_rng(seed)
     edge = voxel * block
@@ -157,14 +160,15 @@ def tsdf_block_frames(n_frames: int = 200, seed: int = 0, voxel: float = 0.006, 
     centre = np.array([5.0, 5.0, 1.5])
     for f in range(n_frames):
         t = f / max(1, n_frames)
-        phases = phases0 + 0.05 * f
+        phases = phases0 + drift * f
         field_ = np.zeros_like(u)
         for j in range(8):
             field_ += amps[j] * np.sin(2 * np.pi * (freqs[j, 0] * u / cam.width + freqs[j, 1] * v / cam.height) + phases[j])
         field_ = (field_ - field_.min()) / max(1e-9, field_.max() - field_.min())
         depth = 0.5 + 3.5 * field_
-        pos = centre + np.array([2.0 * math.cos(2 * np.pi * t), 2.0 * math.sin(2 * np.pi * t), 0.2 * math.sin(4 * np.pi * t)])
-        rot = _rotation(2 * np.pi * t + 0.3 * math.sin(6 * np.pi * t), 0.1 * math.sin(2 * np.pi * t))
+        pos = centre + np.array([orbit * math.cos(2 * np.pi * t), orbit * math.sin(2 * np.pi * t),
+                                 0.1 * math.sin(4 * np.pi * t)])
+        rot = _rotation(2 * np.pi * turn * t + 0.05 * math.sin(6 * np.pi * t), 0.05 * math.sin(2 * np.pi * t))
         xc = (u - cam.cx) * depth / cam.fx
         yc = (v - cam.cy) * depth / cam.fy
         pc = np.stack([xc, yc, depth], axis=1)

@@ -473,3 +473,44 @@ def test_torch_allocator_hook():
         del hm
     finally:
         ash.use_torch_allocator(False)
+
+
+# ------------------------------------------------------ neighbours / export
+@pytest.mark.parametrize("d,radius", [(3, 1), (3, 2), (2, 1), (4, 1), (3, 0)])
+def test_find_neighbors_matches_materialised_queries(d, radius):
+    """Radius neighbour query (Sec. 6.2): the fused kernel equals the oracle's
+    find over the materialised keys q + offset, offsets row-major."""
+    rng = np.random.default_rng(31 + d + radius)
+    keys = rng.integers(-20, 20, size=(6000, d)).astype(np.int32)
+    hm = ash.HashMap(d, 8192)
+    om = oracle.OracleMap(d, 8192)
+    hm.activate(dev(keys))
+    om.activate(keys)
+    q = rng.integers(-22, 22, size=(1001, d)).astype(np.int32)
+    q[:3] = np.array([[2**31 - 1] * d, [-2**31] * d, [0] * d], np.int32)  # int32 wrap-around at the edges
+    gi, gm = hm.find_neighbors(dev(q), radius)
+    offs = workloads.radius_offsets(radius, d)
+    mq = (q[:, None, :].astype(np.int64) + offs[None, :, :]).astype(np.int64)
+    mq = ((mq + 2**31) % 2**32 - 2**31).astype(np.int32).reshape(-1, d)
+    oi, omask = om.find(mq)
+    assert gi.shape == (len(q), len(offs))
+    assert_op_parity(hm, mq, gi.reshape(-1), gm.reshape(-1), oi, omask, check_distinct=False)
+
+
+def test_gather_values_and_export_roundtrip():
+    rng = np.random.default_rng(41)
+    keys = rng.integers(-100, 100, size=(20_000, 3)).astype(np.int32)
+    v0 = rng.standard_normal((20_000, 8, 8, 8)).astype(np.float32)
+    v1 = rng.integers(0, 255, size=(20_000, 3)).astype(np.uint8)
+    hm = ash.HashMap(3, 1 << 15, [(8, 8, 8), (3,)], [torch.float32, torch.uint8])
+    om = oracle.OracleMap(3, 1 << 15, [2048, 3])
+    hm.insert(dev(keys), [dev(v0), dev(v1)])
+    om.insert(keys, [v0, v1])
+    act = hm.active_indices()
+    g0 = hm.gather_values(act, 0)
+    assert torch.equal(g0, hm.value_buffer(0)[act.long()])
+    bad = hm.gather_values(torch.tensor([-1, 1 << 20], dtype=torch.int32, device="cuda"), 1)
+    assert (bad == 0).all()
+    state = hm.export()
+    hm2 = ash.HashMap.from_export(state)
+    assert_same_map(hm2, om)
