@@ -168,6 +168,21 @@ ash_status ash_erase_noalloc(ash_map* map, const int32_t* keys, int64_t n, uint8
 ash_status ash_get_active_indices(ash_map* map, int32_t* out, int64_t out_capacity,
                                   int64_t* count_host, ash_stream stream);
 
+/* Asynchronous listing: as ash_get_active_indices, but enqueued with no host
+ * synchronisation; the live count is written to *count_dev (an int64 in
+ * device memory) when the listing kernels finish.  Pair it with the *_count
+ * gathers below to keep a whole pipeline free of host round trips. */
+ash_status ash_get_active_indices_async(ash_map* map, int32_t* out, int64_t out_capacity, int64_t* count_dev,
+                                        ash_stream stream);
+
+/* Gathers of key rows / value rows (as ash_gather_keys / ash_gather_values)
+ * over min(n_max, *n_dev) indices, n_dev being an int64 in device memory
+ * (e.g. the count of ash_get_active_indices_async). */
+ash_status ash_gather_keys_count(ash_map* map, const int32_t* indices, int64_t n_max, const int64_t* n_dev,
+                                 int32_t* out, ash_stream stream);
+ash_status ash_gather_values_count(ash_map* map, int j, const int32_t* indices, int64_t n_max, const int64_t* n_dev,
+                                   void* out, ash_stream stream);
+
 /* Number of live entries (the heap top t).  Synchronises the stream. */
 ash_status ash_size(ash_map* map, int64_t* size_host, ash_stream stream);
 

@@ -85,6 +85,9 @@ _SIGS = {
     "ash_erase_noalloc": (_I32, [_P, _P, _I64, _P, _P]),
     "ash_get_active_indices": (_I32, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "ash_size": (_I32, [_P, ctypes.POINTER(_I64), _P]),
+    "ash_get_active_indices_async": (_I32, [_P, _P, _I64, _P, _P]),
+    "ash_gather_keys_count": (_I32, [_P, _P, _I64, _P, _P, _P]),
+    "ash_gather_values_count": (_I32, [_P, ctypes.c_int, _P, _I64, _P, _P, _P]),
     "ash_capacity": (_I64, [_P]),
     "ash_key_dim": (ctypes.c_int, [_P]),
     "ash_n_values": (ctypes.c_int, [_P]),
@@ -556,6 +559,21 @@ class HashMap:
         out = torch.empty(max(1, self.capacity()), dtype=torch.int32, device=self.device)
         n = ash_get_active_indices(self._h, out)
         return out[:n]
+
+    def active_indices_async(self):
+        """(indices [capacity] int32, count [1] int64), both on the device, with
+        no host synchronisation; indices[:count] are the live entries."""
+        out = torch.empty(max(1, self.capacity()), dtype=torch.int32, device=self.device)
+        count = torch.empty(1, dtype=torch.int64, device=self.device)
+        _check(lib().ash_get_active_indices_async(self._h, _ptr(out), out.numel(), _ptr(count), _stream(self.device)))
+        return out, count
+
+    def gather_keys_count(self, indices, count):
+        """[len(indices), key_dim] key rows; only the first *count (device) rows are written."""
+        out = torch.empty((indices.numel(), self.key_dim), dtype=torch.int32, device=self.device)
+        _check(lib().ash_gather_keys_count(self._h, _ptr(indices), indices.numel(), _ptr(count), _ptr(out),
+                                           _stream(self.device)))
+        return out
 
     def size(self):
         return ash_size(self._h, _stream(self.device))

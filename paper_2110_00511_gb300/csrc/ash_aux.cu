@@ -122,6 +122,13 @@ void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L)
   set_top_used_kernel<<<1, 1, 0, L.stream>>>(ctrl, v);
 }
 
+__global__ void copy_count_kernel(const Ctrl* ctrl, long long* out) { *out = static_cast<long long>(ctrl->count); }
+
+void launch_copy_count(const Ctrl* ctrl, long long* out, const Launch& L) {
+  TraceScope ts(kKSetCtrl, L.stream);
+  copy_count_kernel<<<1, 1, 0, L.stream>>>(ctrl, out);
+}
+
 // -------------------------------------------------------------- value rows
 // Warp per input position: rows of winners (mask[p] == 1) are copied from
 // src_j + p*row to dst_j + idx[p]*row, 32 lanes x vec bytes per step.
@@ -175,8 +182,12 @@ void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, con
 // --------------------------------------------------------------- key gather
 // Thread per output row: out[r, 0:d] = kB(indices[r]) (zeros for indices
 // outside [0, capacity)).
+// n_dev (optional): the number of rows on the device; the kernel gathers
+// min(n, *n_dev) rows, so a gather can follow an asynchronous listing.
 __global__ void gather_keys_kernel(const int32_t* __restrict__ kb, int ks, int d, int64_t capacity,
-                                   const int32_t* __restrict__ indices, int64_t n, int32_t* __restrict__ out) {
+                                   const int32_t* __restrict__ indices, int64_t n,
+                                   const long long* __restrict__ n_dev, int32_t* __restrict__ out) {
+  if (n_dev) n = min(n, static_cast<int64_t>(*n_dev));
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
     const int32_t i = __ldg(indices + r);
@@ -194,17 +205,19 @@ __global__ void gather_keys_kernel(const int32_t* __restrict__ kb, int ks, int d
 }
 
 void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, const int32_t* indices, int64_t n,
-                        int32_t* out, const Launch& L) {
+                        const long long* n_dev, int32_t* out, const Launch& L) {
   if (n == 0) return;
   TraceScope ts(kKGatherKeys, L.stream);
-  gather_keys_kernel<<<grid_for(n, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, out);
+  gather_keys_kernel<<<grid_for(n, L), L.block, 0, L.stream>>>(kb, ks, d, capacity, indices, n, n_dev, out);
 }
 
 // Warp per output row: out row r <- value buffer row indices[r] (zeros for
 // indices outside [0, capacity)).
 __global__ void __launch_bounds__(256) gather_values_kernel(const char* __restrict__ src, int64_t row_bytes, int vec,
                                                             int64_t capacity, const int32_t* __restrict__ indices,
-                                                            int64_t n, char* __restrict__ out) {
+                                                            int64_t n, const long long* __restrict__ n_dev,
+                                                            char* __restrict__ out) {
+  if (n_dev) n = min(n, static_cast<int64_t>(*n_dev));
   const int lane = threadIdx.x & 31;
   const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
@@ -219,13 +232,13 @@ __global__ void __launch_bounds__(256) gather_values_kernel(const char* __restri
 }
 
 void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t capacity, const int32_t* indices,
-                          int64_t n, void* out, const Launch& L) {
+                          int64_t n, const long long* n_dev, void* out, const Launch& L) {
   if (n == 0) return;
   TraceScope ts(kKGatherValues, L.stream);
   int64_t g = (n * 32 + L.block - 1) / L.block;
   if (g > L.grid_cap) g = L.grid_cap;
   gather_values_kernel<<<static_cast<int>(g < 1 ? 1 : g), L.block, 0, L.stream>>>(
-      static_cast<const char*>(src), row_bytes, vec, capacity, indices, n, static_cast<char*>(out));
+      static_cast<const char*>(src), row_bytes, vec, capacity, indices, n, n_dev, static_cast<char*>(out));
 }
 
 // ------------------------------------------------------------- quantisation

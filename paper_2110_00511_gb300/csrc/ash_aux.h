@@ -22,9 +22,10 @@ void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);
 void launch_scatter_rows(const ValueCopy& vc, const int32_t* idx, const uint8_t* mask, int64_t n, const Launch& L);
 void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, const Launch& L);
 void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, const int32_t* indices, int64_t n,
-                        int32_t* out, const Launch& L);
+                        const long long* n_dev, int32_t* out, const Launch& L);
 void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t capacity, const int32_t* indices,
-                          int64_t n, void* out, const Launch& L);
+                          int64_t n, const long long* n_dev, void* out, const Launch& L);
+void launch_copy_count(const Ctrl* ctrl, long long* out, const Launch& L);
 void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L);
 void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
                   int64_t sink_len, const Launch& L);

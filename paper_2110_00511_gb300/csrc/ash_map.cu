@@ -703,6 +703,49 @@ ash_status ash_get_active_indices(ash_map* m, int32_t* out, int64_t out_capacity
   return ASH_OK;
 }
 
+ash_status ash_get_active_indices_async(ash_map* m, int32_t* out, int64_t out_capacity, int64_t* count_dev,
+                                        ash_stream stream) {
+  if (!m || !count_dev) return fail(ASH_ERR_INVALID, "map and count_dev are required");
+  if (out_capacity > 0 && !out) return fail(ASH_ERR_INVALID, "out is NULL");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  ash_status s = ensure_list_scratch(m, st);
+  if (s != ASH_OK) return s;
+  const ash::Launch L = launch_of(m, st);
+  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0), L);
+  ash::launch_copy_count(m->ctrl, reinterpret_cast<long long*>(count_dev), L);
+  return check_launch("get_active_indices_async");
+}
+
+ash_status ash_gather_keys_count(ash_map* m, const int32_t* indices, int64_t n_max, const int64_t* n_dev,
+                                 int32_t* out, ash_stream stream) {
+  if (!m || !n_dev) return fail(ASH_ERR_INVALID, "map and n_dev are required");
+  if (n_max < 0) return fail(ASH_ERR_INVALID, "n_max must be >= 0");
+  if (n_max == 0) return ASH_OK;
+  if (!indices || !out) return fail(ASH_ERR_INVALID, "indices and out are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ash::launch_gather_keys(m->kb, m->ks, m->key_dim, m->capacity, indices, n_max,
+                          reinterpret_cast<const long long*>(n_dev), out, launch_of(m, st));
+  return check_launch("gather_keys_count");
+}
+
+ash_status ash_gather_values_count(ash_map* m, int j, const int32_t* indices, int64_t n_max, const int64_t* n_dev,
+                                   void* out, ash_stream stream) {
+  if (!m || !n_dev) return fail(ASH_ERR_INVALID, "map and n_dev are required");
+  if (j < 0 || j >= m->n_values) return fail(ASH_ERR_INVALID, "value buffer index out of range");
+  if (n_max < 0) return fail(ASH_ERR_INVALID, "n_max must be >= 0");
+  if (n_max == 0) return ASH_OK;
+  if (!indices || !out) return fail(ASH_ERR_INVALID, "indices and out are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t rb = m->row_bytes[j];
+  ash::launch_gather_values(m->vb[j], rb, vec_width(rb, m->vb[j], out), m->capacity, indices, n_max,
+                            reinterpret_cast<const long long*>(n_dev), out, launch_of(m, st));
+  return check_launch("gather_values_count");
+}
+
 ash_status ash_size(ash_map* m, int64_t* size_host, ash_stream stream) {
   if (!m || !size_host) return fail(ASH_ERR_INVALID, "map and size_host are required");
   DeviceGuard g(m->device);
@@ -792,7 +835,7 @@ ash_status ash_gather_keys(ash_map* m, const int32_t* indices, int64_t n, int32_
   if (!indices || !out) return fail(ASH_ERR_INVALID, "indices and out are required");
   DeviceGuard g(m->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  ash::launch_gather_keys(m->kb, m->ks, m->key_dim, m->capacity, indices, n, out, launch_of(m, st));
+  ash::launch_gather_keys(m->kb, m->ks, m->key_dim, m->capacity, indices, n, nullptr, out, launch_of(m, st));
   return check_launch("gather_keys");
 }
 
@@ -805,7 +848,8 @@ ash_status ash_gather_values(ash_map* m, int j, const int32_t* indices, int64_t 
   DeviceGuard g(m->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t rb = m->row_bytes[j];
-  ash::launch_gather_values(m->vb[j], rb, vec_width(rb, m->vb[j], out), m->capacity, indices, n, out, launch_of(m, st));
+  ash::launch_gather_values(m->vb[j], rb, vec_width(rb, m->vb[j], out), m->capacity, indices, n, nullptr, out,
+                            launch_of(m, st));
   return check_launch("gather_values");
 }
 

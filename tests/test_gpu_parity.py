@@ -514,3 +514,26 @@ def test_gather_values_and_export_roundtrip():
     state = hm.export()
     hm2 = ash.HashMap.from_export(state)
     assert_same_map(hm2, om)
+
+
+def test_async_listing_and_count_gathers():
+    """Listing with the live count left on the device, and gathers bounded by
+    that device count, equal the synchronising forms."""
+    rng = np.random.default_rng(51)
+    keys = rng.integers(-60, 60, size=(50_000, 3)).astype(np.int32)
+    vals = rng.random(50_000, dtype=np.float32)
+    hm = ash.HashMap(3, 60_000, [(1,)], [torch.float32])
+    hm.insert(dev(keys), [dev(vals)])
+    hm.erase(dev(keys[:9000]))
+    act_sync = hm.active_indices()
+    act, cnt = hm.active_indices_async()
+    n = int(cnt.item())
+    assert n == act_sync.numel() == hm.size()
+    assert torch.equal(torch.sort(act[:n]).values, torch.sort(act_sync).values)
+    g = hm.gather_keys_count(act, cnt)
+    assert torch.equal(g[:n], hm.gather_keys(act[:n]))
+    out = torch.full((act.numel(), 1), -1.0, device="cuda")
+    from paper_2110_00511_gb300.ash import lib, _ptr, _stream, _check
+    _check(lib().ash_gather_values_count(hm.handle, 0, _ptr(act), act.numel(), _ptr(cnt), _ptr(out), _stream()))
+    assert torch.equal(out[:n], hm.gather_values(act[:n]))
+    assert bool((out[n:] == -1.0).all()), "rows past the device count must not be written"
