@@ -31,8 +31,13 @@ void launch_erase_resolve(int S, const TableView& t, int64_t n, const int32_t* s
 constexpr int kListThreads = 256;
 constexpr int kListWordsPerBlock = kListThreads;  // one bitmap word (32 indices) per thread
 
-__global__ void mark_free_kernel(const int32_t* __restrict__ heap, int64_t capacity, const Ctrl* __restrict__ ctrl,
+// Also resets the listing counters that compact_live_kernel accumulates into.
+__global__ void mark_free_kernel(const int32_t* __restrict__ heap, int64_t capacity, Ctrl* __restrict__ ctrl,
                                  uint32_t* __restrict__ words) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->count = 0;
+    ctrl->pad1 = 0;  // blocks of the compaction that have finished
+  }
   const int64_t t = static_cast<int64_t>(static_cast<uint32_t>(ctrl->top_used));
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t j = t + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < capacity; j += stride) {
@@ -41,14 +46,18 @@ __global__ void mark_free_kernel(const int32_t* __restrict__ heap, int64_t capac
   }
 }
 
-__global__ void __launch_bounds__(kListThreads) compact_live_kernel(const uint32_t* __restrict__ words,
-                                                                    int64_t capacity, Ctrl* ctrl,
-                                                                    int32_t* __restrict__ out, int64_t out_cap) {
+// Reads and re-zeroes its bitmap words (so the next listing needs no
+// clearing pass).  The last block to finish copies the total to *count_out
+// when given (the live count, left on the device for asynchronous callers).
+__global__ void __launch_bounds__(kListThreads) compact_live_kernel(uint32_t* __restrict__ words, int64_t capacity,
+                                                                    Ctrl* ctrl, int32_t* __restrict__ out,
+                                                                    int64_t out_cap, long long* count_out) {
   __shared__ int s_warp[33];
   __shared__ unsigned long long s_base;
   const int lane = threadIdx.x & 31;
   const int64_t wi = static_cast<int64_t>(blockIdx.x) * kListThreads + threadIdx.x;
   uint32_t live = ~words[wi];
+  words[wi] = 0u;
   const int64_t lo = wi * 32;
   if (lo >= capacity) live = 0;
   else if (lo + 32 > capacity) live &= (1u << (capacity - lo)) - 1u;
@@ -68,6 +77,14 @@ __global__ void __launch_bounds__(kListThreads) compact_live_kernel(const uint32
       if (dst < out_cap) out[dst] = static_cast<int32_t>((w0 + w) * 32 + lane);
     }
   }
+  if (count_out != nullptr && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long done = atomicAdd(&ctrl->pad1, 1ull);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      *count_out = static_cast<long long>(atomicAdd(&ctrl->count, 0ull));
+    }
+  }
 }
 
 int64_t list_scratch_words(int64_t capacity) {
@@ -78,28 +95,35 @@ int64_t list_scratch_words(int64_t capacity) {
 int64_t list_scratch_bytes(int64_t capacity) { return list_scratch_words(capacity) * 4; }
 
 void launch_list_active(const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch, int32_t* out,
-                        int64_t out_cap, const Launch& L) {
+                        int64_t out_cap, long long* count_out, const Launch& L) {
   const int64_t words = list_scratch_words(capacity);
   const int n_blocks = static_cast<int>(words / kListWordsPerBlock);
-  uint32_t* bitmap = static_cast<uint32_t*>(scratch);
+  uint32_t* bitmap = static_cast<uint32_t*>(scratch);  // all zero between listings
   TraceScope ts(kKListActive, L.stream, 2);
-  cudaMemsetAsync(bitmap, 0, words * 4, L.stream);
-  cudaMemsetAsync(&ctrl->count, 0, sizeof(unsigned long long), L.stream);
-  mark_free_kernel<<<grid_for(capacity, L), L.block, 0, L.stream>>>(heap, capacity, ctrl, bitmap);
-  compact_live_kernel<<<n_blocks, kListThreads, 0, L.stream>>>(bitmap, capacity, ctrl, out, out_cap);
+  const int64_t free_max = capacity;  // the kernel starts at the device-side heap top
+  mark_free_kernel<<<grid_for(free_max, L), L.block, 0, L.stream>>>(heap, capacity, ctrl, bitmap);
+  compact_live_kernel<<<n_blocks, kListThreads, 0, L.stream>>>(bitmap, capacity, ctrl, out, out_cap, count_out);
 }
 
 // ------------------------------------------------------------------- heap
+// h[i] = i for i in [from, to): scalar head and tail, int4 stores between.
 __global__ void iota_kernel(int32_t* __restrict__ h, int64_t from, int64_t to) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t i = from + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < to; i += stride)
-    h[i] = static_cast<int32_t>(i);
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t a = min(to, (from + 3) & ~int64_t{3});  // first multiple of 4
+  const int64_t b = max(a, to & ~int64_t{3});
+  for (int64_t i = from + tid; i < a; i += stride) h[i] = static_cast<int32_t>(i);
+  for (int64_t q = a / 4 + tid; q < b / 4; q += stride) {
+    const int32_t v = static_cast<int32_t>(4 * q);
+    reinterpret_cast<int4*>(h)[q] = make_int4(v, v + 1, v + 2, v + 3);
+  }
+  for (int64_t i = b + tid; i < to; i += stride) h[i] = static_cast<int32_t>(i);
 }
 
 void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L) {
   if (to <= from) return;
   TraceScope ts(kKIota, L.stream);
-  iota_kernel<<<grid_for(to - from, L), L.block, 0, L.stream>>>(h, from, to);
+  iota_kernel<<<grid_for((to - from + 3) / 4, L), L.block, 0, L.stream>>>(h, from, to);
 }
 
 __global__ void set_top_used_kernel(Ctrl* ctrl, unsigned long long top_used) { ctrl->top_used = top_used; }
@@ -120,13 +144,6 @@ void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L)
   const unsigned long long v = (static_cast<unsigned long long>(used) << 32) | static_cast<unsigned long long>(top);
   TraceScope ts(kKSetCtrl, L.stream);
   set_top_used_kernel<<<1, 1, 0, L.stream>>>(ctrl, v);
-}
-
-__global__ void copy_count_kernel(const Ctrl* ctrl, long long* out) { *out = static_cast<long long>(ctrl->count); }
-
-void launch_copy_count(const Ctrl* ctrl, long long* out, const Launch& L) {
-  TraceScope ts(kKSetCtrl, L.stream);
-  copy_count_kernel<<<1, 1, 0, L.stream>>>(ctrl, out);
 }
 
 // -------------------------------------------------------------- value rows

@@ -14,8 +14,10 @@ struct Launch;
 // part of the heap).  scratch: list_scratch_bytes(capacity) bytes of device
 // memory.  Writes at most out_cap indices; the live count goes to ctrl->count.
 int64_t list_scratch_bytes(int64_t capacity);
+// count_out (optional): device int64 receiving the live count.  The scratch
+// bitmap must be zero on entry; the listing leaves it zero.
 void launch_list_active(const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch, int32_t* out,
-                        int64_t out_cap, const Launch& L);
+                        int64_t out_cap, long long* count_out, const Launch& L);
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L);
 void launch_set_used_from_count(Ctrl* ctrl, const Launch& L);
 void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);
@@ -25,7 +27,6 @@ void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, cons
                         const long long* n_dev, int32_t* out, const Launch& L);
 void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t capacity, const int32_t* indices,
                           int64_t n, const long long* n_dev, void* out, const Launch& L);
-void launch_copy_count(const Ctrl* ctrl, long long* out, const Launch& L);
 void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L);
 void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
                   int64_t sink_len, const Launch& L);

@@ -283,6 +283,7 @@ ash_status ensure_list_scratch(ash_map* m, cudaStream_t st) {
     return fail(ASH_ERR_OOM, "listing scratch allocation failed");
   }
   m->list_scratch_bytes = need;
+  ASH_CUDA(cudaMemsetAsync(m->list_scratch, 0, need, st));  // each listing leaves it zero again
   return ASH_OK;
 }
 
@@ -298,7 +299,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
     dev_free(m, list, st);
     return s;
   }
-  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, list, size, L);
+  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, list, size, nullptr, L);
   s = check_launch("rehash listing");
   if (s != ASH_OK) return s;
 
@@ -400,7 +401,7 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
     dev_free(m, list, st);
     return s;
   }
-  ash::launch_list_active(m->heap, c, m->ctrl, m->list_scratch, list, c, L);
+  ash::launch_list_active(m->heap, c, m->ctrl, m->list_scratch, list, c, nullptr, L);
   const int64_t n_slots = slots_for(new_capacity, m->tuning);
   if (n_slots >= (int64_t{1} << 31)) {
     dev_free(m, list, st);
@@ -693,7 +694,7 @@ ash_status ash_get_active_indices(ash_map* m, int32_t* out, int64_t out_capacity
   ash_status s = ensure_list_scratch(m, st);
   if (s != ASH_OK) return s;
   ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
-                          launch_of(m, st));
+                          nullptr, launch_of(m, st));
   s = check_launch("get_active_indices");
   if (s != ASH_OK) return s;
   int64_t top, used;
@@ -713,8 +714,8 @@ ash_status ash_get_active_indices_async(ash_map* m, int32_t* out, int64_t out_ca
   ash_status s = ensure_list_scratch(m, st);
   if (s != ASH_OK) return s;
   const ash::Launch L = launch_of(m, st);
-  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0), L);
-  ash::launch_copy_count(m->ctrl, reinterpret_cast<long long*>(count_dev), L);
+  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
+                          reinterpret_cast<long long*>(count_dev), L);
   return check_launch("get_active_indices_async");
 }
 
