@@ -326,15 +326,27 @@ def main(argv=None):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
 
+    aux = torch.cuda.Stream(device=device)
+
     def step(points, keys_out):
-        # no host synchronisation anywhere in the step: the live count stays on
-        # the device and bounds the gather of the unique voxel keys
+        # No host synchronisation anywhere in the step: the live count stays on
+        # the device and bounds the gather of the unique voxel keys.  Two
+        # streams overlap independent work: the map is created (table fill,
+        # heap init) while the points are quantised, and the live entries are
+        # listed and gathered while every point finds its voxel.
+        main = torch.cuda.current_stream(device)
+        aux.wait_stream(main)
+        with torch.cuda.stream(aux):
+            hm = ash.HashMap(3, N, [(1,)], [torch.int32], device=device)
         ash.ash_quantize(points, args.voxel, out=keys_out)
-        hm = ash.HashMap(3, N, [(1,)], [torch.int32], device=device)
+        main.wait_stream(aux)
         idx, mask = hm.insert(keys_out, [point_ids])
-        fidx, fmask = hm.find(keys_out)
-        act, count = hm.active_indices_async()
-        uniq = hm.gather_keys_count(act, count)
+        aux.wait_stream(main)
+        with torch.cuda.stream(aux):
+            act, count = hm.active_indices_async()
+            uniq = hm.gather_keys_count(act, count)
+        fidx, fmask = hm.find(keys_out)  # last call on the main stream
+        main.wait_stream(aux)            # join before the map is freed on the main stream
         del hm
         return fidx, uniq, count
 
@@ -480,8 +492,8 @@ def main(argv=None):
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "points": N, "voxel_m": args.voxel, "key_dim": 3,
                            "unique_voxels": n_unique, "value": "int32 point index",
-                           "step": "quantize, create, insert, find, list active, gather unique keys, destroy "
-                                   "(no host synchronisation inside a step)",
+                           "step": "quantize || create, insert, find || (list active, gather unique keys), destroy "
+                                   "(two streams, no host synchronisation inside a step)",
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -110,7 +110,9 @@ ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t
                       const int32_t* value_dtypes_host, int device, const ash_tuning* tuning,
                       ash_stream stream, ash_map** out_host);
 
-/* Frees every buffer of the map (on the stream of its last call). */
+/* Frees every buffer of the map, stream-ordered on the stream of its last
+ * call.  Work that used the map on other streams must be ordered before that
+ * stream first (e.g. make it wait on those streams). */
 ash_status ash_destroy(ash_map* map);
 
 /* Lazy insertion (Sec. 4.3.1) of n keys with their values.
