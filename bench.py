@@ -12,6 +12,7 @@ Metric value = hash ops (insert + find keys) per second over the timed steps.
 workload instead (the reference arm of this comparison).
 """
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -38,7 +39,7 @@ WORKLOAD = ("point-cloud voxelization: 4M float32 points on 32 spheres + 3 plane
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--points", type=int, default=4_000_000)
@@ -103,7 +104,7 @@ def barrier(world):
 class ClockSampler:
     """Samples SM clock and throttle reasons with nvidia-smi while running."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -111,6 +112,10 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.window = None  # (start, end) wall-clock seconds of the timed region
+
+    def mark(self, start, end):
+        self.window = (start, end)
 
     def __enter__(self):
         try:
@@ -118,7 +123,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -137,20 +142,27 @@ class ClockSampler:
         rows = []
         for ln in open(self.path):
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((float(parts[2]), float(parts[3]), parts[5:10], ts))
             except ValueError:
                 continue
         os.unlink(self.path)
+        if self.window is not None:
+            inside = [r for r in rows if self.window[0] - 0.06 <= r[3] <= self.window[1] + 0.06]
+            in_window = bool(inside)
+            rows = inside or rows
+        else:
+            in_window = False
         if not rows:
             return None
         sm = [r[0] for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2][1:]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "samples_in_timed_region": in_window, "interval_ms": 50}
 
 
 # ------------------------------------------------------ algorithmic bytes
@@ -198,10 +210,14 @@ def bytes_erase(n_present, n_absent, d=3):
     return bytes_find(n_present, n_absent, d) + n_present * 36
 
 
+# The sources the insert claim / insert commit / find kernels compile from.
+KERNEL_SOURCES = ("ash_device.cuh", "ash_kernels.cuh", "ash_dim.cu")
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_00511_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -365,6 +381,7 @@ def main(argv=None):
     barrier(world)
     torch.cuda.synchronize()
     launches0 = ash.ash_kernel_launch_count()
+    t_wall0 = time.time()
     gc.disable()
     ash.ash_trace_enable(True)
     for s in range(args.steps):
@@ -374,8 +391,10 @@ def main(argv=None):
         ends[s].record(stream)
     ash.ash_trace_enable(False)
     torch.cuda.synchronize()
+    t_wall1 = time.time()
     n_unique = int(count.item())
     gc.enable()
+    clocks.mark(t_wall0, t_wall1)
     clocks.__exit__(None, None, None)
     barrier(world)
     launches = ash.ash_kernel_launch_count() - launches0
@@ -413,26 +432,61 @@ def main(argv=None):
                 "unit": "GB/s", "frac": dk["achieved_gbs"] / hbm_peak,
                 "traffic": measured_traffic(dominant)}
 
-    # ------------------------------------------------- random-read roofline
+    # ----------------------------------------------- random-access rooflines
+    # Measured by the library's own probe kernels: random sector reads at the
+    # step's table footprint (64 MB), at 512 MiB and at 8 GiB; random 64-bit
+    # CAS and the claim's load->CAS chain at the table footprint.  The insert
+    # claim is bound by the atomic chain, the find by random reads.
     probe = None
     try:
         if args.lean:
             raise RuntimeError("skipped (--lean)")
-        buf = torch.empty(8 << 30, dtype=torch.uint8, device=device)
         sink = torch.zeros(4096, dtype=torch.int32, device=device)
-        n_reads = 1 << 28
-        for sector in (32, 64):
-            for _ in range(2):
-                ash.ash_probe_random_read(buf, n_reads // 8, sector, sink, seed=1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ash.ash_probe_random_read(buf, n_reads, sector, sink, seed=7)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            probe = probe or {}
-            probe[f"random_{sector}B_gbs"] = n_reads * sector / (ms / 1000) / 1e9
-        del buf
+        probe = {}
+
+        def timed_probe(fn, reps=3):
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            return best
+
+        table_bytes = 16 * N  # 2 slots of 8 bytes per unit of capacity
+        for label, nbytes in (("table", table_bytes), ("512MiB", 512 << 20), ("8GiB", 8 << 30)):
+            buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            n_reads = 1 << 26
+            ms = timed_probe(lambda: ash.ash_probe_random_read(buf, n_reads, 32, sink, seed=7))
+            probe[f"read32_{label}_Gops"] = n_reads / (ms / 1000) / 1e9
+            probe[f"read32_{label}_GBps"] = n_reads * 32 / (ms / 1000) / 1e9
+            del buf
+        tbl = torch.empty(table_bytes, dtype=torch.uint8, device=device)
+        n_ops = N
+        for mode, label in ((0, "cas_table_Gops"), (1, "load_cas_chain_table_Gops")):
+            # the slots start all ones (EMPTY); the fill stays outside the events
+            best = None
+            for _ in range(3):
+                tbl.fill_(255)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ash.ash_probe_random_atomic(tbl, n_ops, mode, sink, seed=11)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            probe[label] = n_ops / (best / 1000) / 1e9
+        del tbl
+        claim_rate = N / (kernels["insert_claim"]["ms_per_launch"] / 1000) / 1e9
+        find_sectors = 2 * N / (kernels["find"]["ms_per_launch"] / 1000) / 1e9
+        probe["insert_claim_Gkeys"] = claim_rate
+        probe["insert_claim_frac_of_load_cas_chain"] = claim_rate / probe["load_cas_chain_table_Gops"]
+        probe["find_random_sectors_G"] = find_sectors
+        probe["find_frac_of_read32_table"] = find_sectors / probe["read32_table_Gops"]
     except Exception as e:  # noqa: BLE001
         probe = {"error": str(e)[:200]}
 
@@ -497,7 +551,7 @@ def main(argv=None):
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks.summary(), "kernels": kernels, "random_read_roofline": probe,
+                "clocks": clocks.summary(), "kernels": kernels, "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "ops": ops, "batched": batched, "serving": serving, "source_digest": source_digest()}
         print(json.dumps(line), flush=True)

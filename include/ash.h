@@ -240,6 +240,15 @@ ash_status ash_gather_values(ash_map* map, int j, const int32_t* indices, int64_
 ash_status ash_find_neighbors(ash_map* map, const int32_t* keys, int64_t n, int32_t radius, int32_t* buf_indices,
                               uint8_t* masks, ash_stream stream);
 
+/* Neighbour query over an explicit offset table: the 1-radius (3^d), 1-cube
+ * (2^d, the grid points enclosing a cell) and 1-ring (the 2d face
+ * neighbours) tables of Sec. 6.2 and Sec. 6.4, or any other.  offsets is
+ * [n_offsets, key_dim] int32 in device memory (1 <= n_offsets <= 4096);
+ * entry [r, m] of buf_indices / masks ([n, n_offsets]) is the masked query
+ * (Eq. (4)) of keys[r] + offsets[m] (int32 wrap-around). */
+ash_status ash_find_offsets(ash_map* map, const int32_t* keys, int64_t n, const int32_t* offsets, int64_t n_offsets,
+                            int32_t* buf_indices, uint8_t* masks, ash_stream stream);
+
 ash_status ash_get_tuning(const ash_map* map, ash_tuning* out_host);
 ash_status ash_set_tuning(ash_map* map, const ash_tuning* tuning_host);
 
@@ -367,6 +376,15 @@ ash_status ash_trace_collect(void);
 ash_status ash_trace_read(int kind, double* total_ms_host, int64_t* launches_host);
 ash_status ash_trace_reset(void);
 uint64_t ash_kernel_launch_count(void);
+
+/* Random-atomic probe (measurement only, not part of the map): n_ops 64-bit
+ * CAS operations on buf (buf_bytes, a multiple of 32, 32-byte aligned, read
+ * as 32-byte buckets whose slots must start all ones).  mode 0: a CAS on a
+ * random slot; mode 1: a relaxed 32-byte bucket load followed by a CAS on
+ * the bucket's first all-ones slot (the dependent chain of an insert claim).
+ * Sets the atomic roofline the claim kernel is compared with. */
+ash_status ash_probe_random_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed,
+                                   uint32_t* sink, int64_t sink_len, ash_stream stream);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char* ash_last_error(void);

@@ -101,11 +101,13 @@ _SIGS = {
     "ash_gather_keys": (_I32, [_P, _P, _I64, _P, _P]),
     "ash_gather_values": (_I32, [_P, ctypes.c_int, _P, _I64, _P, _P]),
     "ash_find_neighbors": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "ash_find_offsets": (_I32, [_P, _P, _I64, _P, _I64, _P, _P, _P]),
     "ash_get_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_sync_status": (_I32, [_P, _P]),
     "ash_quantize": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
     "ash_probe_random_read": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
+    "ash_probe_random_atomic": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
     "ash_trace_kernel_kinds": (ctypes.c_int, []),
     "ash_trace_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "ash_trace_enable": (_I32, [ctypes.c_int]),
@@ -322,6 +324,12 @@ def ash_quantize(points, cell, out=None, stream=None):
     _check(lib().ash_quantize(_ptr(points), points.numel(), ctypes.c_float(cell), _ptr(out),
                               stream if stream is not None else _stream(points.device)))
     return out
+
+
+def ash_probe_random_atomic(buf, n_ops, mode, sink, seed=0, stream=None):
+    _check(lib().ash_probe_random_atomic(_ptr(buf), buf.numel() * buf.element_size(), int(n_ops), int(mode),
+                                         ctypes.c_uint32(seed), _ptr(sink), sink.numel(),
+                                         stream if stream is not None else _stream(buf.device)))
 
 
 def ash_probe_random_read(buf, n_reads, sector_bytes, sink, seed=0, stream=None):
@@ -617,6 +625,17 @@ class HashMap:
         mask = torch.empty((keys.shape[0], k), dtype=torch.bool, device=self.device)
         _check(lib().ash_find_neighbors(self._h, _ptr(keys), keys.shape[0], int(radius), _ptr(idx), _ptr(mask),
                                         _stream(self.device)))
+        return idx, mask
+
+    def find_offsets(self, keys, offsets):
+        """Masked queries of keys[r] + offsets[m] for an explicit [n_off, d]
+        offset table: (buf_indices, masks), each [n, n_off]."""
+        keys = self._keys(keys)
+        off = self._keys(offsets)
+        idx = torch.empty((keys.shape[0], off.shape[0]), dtype=torch.int32, device=self.device)
+        mask = torch.empty((keys.shape[0], off.shape[0]), dtype=torch.bool, device=self.device)
+        _check(lib().ash_find_offsets(self._h, _ptr(keys), keys.shape[0], _ptr(off), off.shape[0], _ptr(idx),
+                                      _ptr(mask), _stream(self.device)))
         return idx, mask
 
     def export(self):

@@ -328,6 +328,49 @@ __global__ void __launch_bounds__(256) probe_kernel(const uint64_t* __restrict__
   if (folded == 0x9E3779B9u) sink[slot] = folded;  // practically never taken; keeps the loads live
 }
 
+// Random 64-bit atomics on a table of 32-byte buckets (all slots start
+// EMPTY = all ones).  mode 0: CAS EMPTY -> op id on a random slot;
+// mode 1: the claim chain, a relaxed 32-byte bucket load then a CAS on the
+// bucket's first EMPTY slot.  Each thread keeps one operation in flight.
+template <int MODE>
+__global__ void __launch_bounds__(256) probe_atomic_kernel(uint64_t* __restrict__ slots, uint64_t n_buckets,
+                                                           int64_t n_ops, uint32_t seed, uint32_t* __restrict__ sink,
+                                                           int64_t sink_len) {
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  uint64_t acc = 0;
+  for (int64_t r = tid; r < n_ops; r += nthreads) {
+    const uint64_t b = __umul64hi(mix64(static_cast<uint64_t>(r) * 0x9E3779B97F4A7C15ull + seed), n_buckets);
+    uint64_t* bp = slots + 4 * b;
+    if constexpr (MODE == 0) {
+      const uint32_t s = static_cast<uint32_t>(mix64(static_cast<uint64_t>(r) + seed) & 3u);
+      acc ^= atomicCAS(reinterpret_cast<unsigned long long*>(bp + s), ~0ull, static_cast<unsigned long long>(r));
+    } else {
+      uint64_t w0, w1, w2, w3;
+      load32<false>(bp, w0, w1, w2, w3);
+      int e = w3 == ~0ull ? 3 : 0;
+      e = w2 == ~0ull ? 2 : e;
+      e = w1 == ~0ull ? 1 : e;
+      e = w0 == ~0ull ? 0 : e;
+      acc ^= atomicCAS(reinterpret_cast<unsigned long long*>(bp + e), ~0ull, static_cast<unsigned long long>(r));
+    }
+  }
+  const uint32_t folded = static_cast<uint32_t>(acc ^ (acc >> 32));
+  if (folded == 0x9E3779B9u) sink[tid % sink_len] = folded;  // practically never taken; keeps the atomics live
+}
+
+void launch_probe_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed, uint32_t* sink,
+                         int64_t sink_len, const Launch& L) {
+  const uint64_t n_buckets = static_cast<uint64_t>(buf_bytes) / 32u;
+  TraceScope ts(kKProbe, L.stream);
+  if (mode == 0)
+    probe_atomic_kernel<0><<<L.grid_cap, L.block, 0, L.stream>>>(static_cast<uint64_t*>(buf), n_buckets, n_ops, seed,
+                                                                  sink, sink_len);
+  else
+    probe_atomic_kernel<1><<<L.grid_cap, L.block, 0, L.stream>>>(static_cast<uint64_t*>(buf), n_buckets, n_ops, seed,
+                                                                  sink, sink_len);
+}
+
 void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
                   int64_t sink_len, const Launch& L) {
   const uint64_t n_sectors = static_cast<uint64_t>(buf_bytes) / static_cast<uint64_t>(sector);

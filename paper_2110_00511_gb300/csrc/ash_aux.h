@@ -28,6 +28,8 @@ void launch_gather_keys(const int32_t* kb, int ks, int d, int64_t capacity, cons
 void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t capacity, const int32_t* indices,
                           int64_t n, const long long* n_dev, void* out, const Launch& L);
 void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L);
+void launch_probe_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed, uint32_t* sink,
+                         int64_t sink_len, const Launch& L);
 void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
                   int64_t sink_len, const Launch& L);
 

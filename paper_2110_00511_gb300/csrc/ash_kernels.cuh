@@ -97,6 +97,30 @@ __global__ void __launch_bounds__(256) neighbors_kernel(TableView t, const int32
   }
 }
 
+// Neighbour query over an explicit offset table (the neighbour tables of
+// Sec. 6.2-6.4: 1-radius 3^D, 1-cube 2^D, 1-ring): thread per (query, offset)
+// pair; offsets is [n_off, D] int32 in device memory, added with int32
+// wrap-around.  Outputs are [n, n_off].
+template <int D, int S>
+__global__ void __launch_bounds__(256) offsets_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+                                                      const int32_t* __restrict__ offsets, int64_t n_off,
+                                                      int32_t* __restrict__ idx, uint8_t* __restrict__ mask) {
+  const int64_t total = n * n_off;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t r = e / n_off;
+    const int64_t o = e - r * n_off;
+    int32_t k[D];
+    load_input_key<D>(keys, r, k);
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      k[j] = static_cast<int32_t>(static_cast<uint32_t>(k[j]) + static_cast<uint32_t>(__ldg(offsets + o * D + j)));
+    const int32_t out = find_key<D, S>(t, k);
+    idx[e] = out;
+    mask[e] = out >= 0 ? 1 : 0;
+  }
+}
+
 // KPT keys per thread: positions base, base + blockDim.x, ... so every load
 // instruction stays coalesced across the warp.  All home buckets are loaded
 // before any is examined, and all verify loads are issued before any compare.
@@ -630,6 +654,8 @@ struct DimKernels {
   void (*rebuild)(int S, const TableView&, const int32_t*, const int32_t*, int64_t, const unsigned long long*, int, int,
                   const Launch&);
   void (*neighbors)(int S, const TableView&, const int32_t*, int64_t, int, int64_t, int32_t*, uint8_t*, const Launch&);
+  void (*offsets)(int S, const TableView&, const int32_t*, int64_t, const int32_t*, int64_t, int32_t*, uint8_t*,
+                  const Launch&);
 };
 
 template <int D>
@@ -722,9 +748,22 @@ struct DimLaunchers {
     else if (S == 8) neighbors_s<8>(t, keys, n, radius, n_off, idx, mask, L);
     else neighbors_s<16>(t, keys, n, radius, n_off, idx, mask, L);
   }
+  template <int S>
+  static void offsets_s(const TableView& t, const int32_t* keys, int64_t n, const int32_t* off, int64_t n_off,
+                        int32_t* idx, uint8_t* mask, const Launch& L) {
+    TraceScope ts(kKNeighbors, L.stream);
+    offsets_kernel<D, S><<<grid_for(n * n_off, L), L.block, 0, L.stream>>>(t, keys, n, off, n_off, idx, mask);
+  }
+  static void offsets(int S, const TableView& t, const int32_t* keys, int64_t n, const int32_t* off, int64_t n_off,
+                      int32_t* idx, uint8_t* mask, const Launch& L) {
+    if (S == 4) offsets_s<4>(t, keys, n, off, n_off, idx, mask, L);
+    else if (S == 8) offsets_s<8>(t, keys, n, off, n_off, idx, mask, L);
+    else offsets_s<16>(t, keys, n, off, n_off, idx, mask, L);
+  }
   static DimKernels table() {
     DimKernels k;
     k.neighbors = &neighbors;
+    k.offsets = &offsets;
     k.find = &find;
     k.claim = &claim;
     k.commit = &commit;

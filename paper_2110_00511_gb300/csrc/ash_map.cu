@@ -872,6 +872,22 @@ ash_status ash_find_neighbors(ash_map* m, const int32_t* keys, int64_t n, int32_
   return check_launch("find_neighbors");
 }
 
+ash_status ash_find_offsets(ash_map* m, const int32_t* keys, int64_t n, const int32_t* offsets, int64_t n_offsets,
+                            int32_t* buf_indices, uint8_t* masks, ash_stream stream) {
+  ash_status s = check_keys(m, keys, n);
+  if (s != ASH_OK) return s;
+  if (n_offsets < 1 || n_offsets > 4096) return fail(ASH_ERR_INVALID, "n_offsets must be in 1..4096");
+  if (!offsets) return fail(ASH_ERR_INVALID, "offsets is NULL");
+  if (n * n_offsets >= (int64_t{1} << 40)) return fail(ASH_ERR_INVALID, "too many neighbour queries");
+  if (n == 0) return ASH_OK;
+  if (!buf_indices || !masks) return fail(ASH_ERR_INVALID, "buf_indices and masks are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  m->K.offsets(m->S, view_of(m), keys, n, offsets, n_offsets, buf_indices, masks, launch_of(m, st));
+  return check_launch("find_offsets");
+}
+
 ash_status ash_get_tuning(const ash_map* m, ash_tuning* out_host) {
   if (!m || !out_host) return fail(ASH_ERR_INVALID, "map and out are required");
   *out_host = m->tuning;
@@ -931,6 +947,22 @@ ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_r
   L.grid_cap = sm_count(dev) * 8;
   ash::launch_probe(buf, buf_bytes, n_reads, sector_bytes, seed, sink, sink_len, L);
   return check_launch("probe");
+}
+
+ash_status ash_probe_random_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed,
+                                   uint32_t* sink, int64_t sink_len, ash_stream stream) {
+  if (!buf || !sink || sink_len < 1 || n_ops < 0) return fail(ASH_ERR_INVALID, "bad probe arguments");
+  if (mode != 0 && mode != 1) return fail(ASH_ERR_INVALID, "mode must be 0 or 1");
+  if (buf_bytes < 32 || buf_bytes % 32 != 0) return fail(ASH_ERR_INVALID, "buf_bytes must be a positive multiple of 32");
+  if ((reinterpret_cast<uintptr_t>(buf) & 31u) != 0) return fail(ASH_ERR_INVALID, "buf must be 32-byte aligned");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  ash::Launch L;
+  L.stream = reinterpret_cast<cudaStream_t>(stream);
+  L.block = 256;
+  L.grid_cap = sm_count(dev) * 8;
+  ash::launch_probe_atomic(buf, buf_bytes, n_ops, mode, seed, sink, sink_len, L);
+  return check_launch("probe_atomic");
 }
 
 const char* ash_last_error(void) { return g_last_error.c_str(); }

@@ -184,6 +184,23 @@ def radius_offsets(r: int = 1, key_dim: int = 3) -> np.ndarray:
     return grid.astype(np.int32)
 
 
+def cube_offsets(key_dim: int = 3) -> np.ndarray:
+    """The 2^key_dim grid points of the cell whose lowest corner is the key
+    (the 1-cube table), first coordinate slowest."""
+    axes = [np.arange(0, 2)] * key_dim
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, key_dim)
+    return grid.astype(np.int32)
+
+
+def ring_offsets(key_dim: int = 3) -> np.ndarray:
+    """The 2*key_dim face neighbours (the 1-ring table): -e_0, +e_0, -e_1, ..."""
+    out = np.zeros((2 * key_dim, key_dim), np.int32)
+    for j in range(key_dim):
+        out[2 * j, j] = -1
+        out[2 * j + 1, j] = 1
+    return out
+
+
 # ----------------------------------------------------------------- batched
 @dataclass
 class MapBatch:

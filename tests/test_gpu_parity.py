@@ -537,3 +537,48 @@ def test_async_listing_and_count_gathers():
     _check(lib().ash_gather_values_count(hm.handle, 0, _ptr(act), act.numel(), _ptr(cnt), _ptr(out), _stream()))
     assert torch.equal(out[:n], hm.gather_values(act[:n]))
     assert bool((out[n:] == -1.0).all()), "rows past the device count must not be written"
+
+
+def test_set_intersection_with_a_hash_set():
+    """Set intersection through a hash set (no value buffers, Sec. 4.7):
+    activate A, find B; B's hits are exactly the rows of B that occur in A."""
+    rng = np.random.default_rng(61)
+    a = rng.integers(-50, 50, size=(200_000, 3)).astype(np.int32)
+    b = rng.integers(-60, 60, size=(300_001, 3)).astype(np.int32)
+    hs = ash.HashMap(3, len(a))
+    om = oracle.OracleMap(3, len(a))
+    hs.activate(dev(a))
+    om.activate(a)
+    fi, fm = hs.find(dev(b))
+    ofi, ofm = om.find(b)
+    assert_op_parity(hs, b, fi, fm, ofi, ofm, check_distinct=False)
+    pack = lambda x: (x.astype(np.int64) + 64) @ np.array([1 << 16, 1 << 8, 1], np.int64)  # noqa: E731
+    assert np.array_equal(fm.cpu().numpy().astype(bool), np.isin(pack(b), pack(a)))
+
+
+@pytest.mark.parametrize("table", ["radius1", "cube", "ring", "random"])
+def test_find_offsets_tables(table):
+    """Neighbour tables (1-radius, 1-cube, 1-ring, and an arbitrary table with
+    extreme offsets) equal the oracle's find over the materialised keys."""
+    d = 3
+    rng = np.random.default_rng(71)
+    keys = rng.integers(-16, 16, size=(7000, d)).astype(np.int32)
+    hm = ash.HashMap(d, 8192)
+    om = oracle.OracleMap(d, 8192)
+    hm.activate(dev(keys))
+    om.activate(keys)
+    offs = {"radius1": workloads.radius_offsets(1, d), "cube": workloads.cube_offsets(d),
+            "ring": workloads.ring_offsets(d),
+            "random": np.concatenate([rng.integers(-3, 4, size=(47, d)),
+                                      np.array([[2**31 - 1, 0, 0], [-2**31, 5, -5], [0, 0, 0]])]).astype(np.int32)}[table]
+    q = rng.integers(-18, 18, size=(2049, d)).astype(np.int32)
+    q[:2] = np.array([[2**31 - 1] * d, [-2**31] * d], np.int32)
+    gi, gm = hm.find_offsets(dev(q), dev(offs))
+    mq = (q[:, None, :].astype(np.int64) + offs[None, :, :].astype(np.int64))
+    mq = ((mq + 2**31) % 2**32 - 2**31).astype(np.int32).reshape(-1, d)
+    oi, omask = om.find(mq)
+    assert gi.shape == (len(q), len(offs))
+    assert_op_parity(hm, mq, gi.reshape(-1), gm.reshape(-1), oi, omask, check_distinct=False)
+    if table == "radius1":
+        ri, rm = hm.find_neighbors(dev(q), 1)
+        assert torch.equal(ri, gi) and torch.equal(rm, gm)
