@@ -3,8 +3,10 @@
 A plain sequential hash map written from the paper (arXiv 2110.00511): the
 index-first SoA map of Sec. 4.2, the index heap of Sec. 4.3, lazy insertion of
 Sec. 4.3.1, activate of Sec. 5.1, erase, rehash of Sec. 4.5 and the voxel
-quantisation of Sec. 6.1.  The arithmetic lives in ash_oracle.cpp; this module
-only marshals numpy arrays.
+quantisation of Sec. 6.1.  It also covers the geometry consumers of
+Sec. 6.2: the double hash map block allocation, TSDF integration (Eq. (7)-(9))
+and ray casting.  The arithmetic lives in ash_oracle.cpp; this module only
+marshals numpy arrays.
 
 Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
 legs may import this package.  It shares no code with the CUDA path and never
@@ -48,6 +50,16 @@ def _lib(mutant: int = 0):
         lib.om_copy_values.argtypes = [_ptr, ctypes.c_int, _ptr]
         lib.om_copy_heap.argtypes = [_ptr, _ptr]
         lib.om_quantize.argtypes = [_ptr, _i64, ctypes.c_float, _ptr]
+        lib.om_depth_to_block_keys.restype = _i64
+        lib.om_depth_to_block_keys.argtypes = [_ptr, ctypes.c_int, ctypes.c_int, _ptr, _ptr, ctypes.c_float,
+                                               ctypes.c_float, _ptr]
+        lib.om_double_map_activate.restype = _i64
+        lib.om_double_map_activate.argtypes = [_ptr, _ptr, _ptr, _i64, _ptr, _ptr, _ptr]
+        _f = ctypes.c_float
+        lib.om_tsdf_integrate.argtypes = [_ptr, _ptr, _i64, ctypes.c_int, _ptr, ctypes.c_int, ctypes.c_int, _ptr, _ptr,
+                                          _f, _f, _f]
+        lib.om_tsdf_raycast.argtypes = [_ptr, ctypes.c_int, ctypes.c_int, _ptr, _ptr, ctypes.c_int, _f, _f, _f, _i64,
+                                        _ptr, _i64, _ptr]
         _libs[mutant] = lib
     return _libs[mutant]
 
@@ -167,4 +179,66 @@ def quantize(points, voxel, mutant=0):
     p = _c(points, np.float32)
     out = np.empty(p.shape, np.int32)
     _lib(mutant).om_quantize(p.ctypes.data, p.size, ctypes.c_float(voxel), out.ctypes.data)
+    return out
+
+
+def double_map_activate(local, glob, keys):
+    """Double hash map block allocation (Sec. 6.2): local activate, the
+    distinct new keys in input order, global activate + find, and the local
+    map's int32 value rows := global indices.  Returns (unique_keys [u, d],
+    local_indices [u], global_indices [u])."""
+    k, n = local._keys(keys)
+    uk = np.empty((n, local.key_dim), np.int32)
+    li = np.empty(n, np.int32)
+    gi = np.empty(n, np.int32)
+    u = local._lib.om_double_map_activate(local._h, glob._h, k.ctypes.data, n, uk.ctypes.data, li.ctypes.data,
+                                          gi.ctypes.data)
+    if u < 0:
+        raise RuntimeError("oracle activation failed")
+    return uk[:u].copy(), li[:u].copy(), gi[:u].copy()
+
+
+def _cam(intrinsics, extrinsic):
+    intr = _c(np.asarray(intrinsics, np.float32).reshape(4), np.float32)
+    extr = _c(np.asarray(extrinsic, np.float32).reshape(3, 4), np.float32)
+    return intr, extr
+
+
+def depth_to_block_keys(depth, intrinsics, extrinsic, block_edge, depth_max, mutant=0):
+    """int32 [n, 3] block keys of the pixels with depth in (0, depth_max], in
+    pixel order (Sec. 6.2 unprojection, Eq. (11))."""
+    dep = _c(depth, np.float32)
+    intr, extr = _cam(intrinsics, extrinsic)
+    out = np.empty((dep.size, 3), np.int32)
+    n = _lib(mutant).om_depth_to_block_keys(dep.ctypes.data, dep.shape[1], dep.shape[0], intr.ctypes.data,
+                                            extr.ctypes.data, ctypes.c_float(block_edge), ctypes.c_float(depth_max),
+                                            out.ctypes.data)
+    return out[:n].copy()
+
+
+def tsdf_integrate(om, block_indices, depth, intrinsics, extrinsic, voxel, trunc, depth_max, ell=8):
+    """TSDF integration of one frame (Sec. 6.2, Eq. (7)-(9)) into the blocks at
+    block_indices.  om holds float64 value buffers: 0 = d, 1 = w (ell^3 each).
+    intrinsics = (fx, fy, cx, cy); extrinsic = world-to-camera [R | t] (3x4)."""
+    bi = _c(block_indices, np.int32).reshape(-1)
+    dep = _c(depth, np.float32)
+    intr, extr = _cam(intrinsics, extrinsic)
+    om._lib.om_tsdf_integrate(om._h, bi.ctypes.data, bi.size, int(ell), dep.ctypes.data, dep.shape[1], dep.shape[0],
+                              intr.ctypes.data, extr.ctypes.data, ctypes.c_float(voxel), ctypes.c_float(trunc),
+                              ctypes.c_float(depth_max))
+
+
+def tsdf_raycast(om, intrinsics, extrinsic, width, height, voxel, depth_min, step, n_steps, pixels=None, ell=8,
+                 value_bytes=8):
+    """Ray casting (Sec. 6.2): depth of the first positive-to-negative zero
+    crossing per pixel (0 if none), for the listed pixel ids (py * width + px;
+    all pixels if None).  Returns float64 depths."""
+    if pixels is None:
+        pixels = np.arange(width * height, dtype=np.int64)
+    px = _c(pixels, np.int64).reshape(-1)
+    out = np.empty(px.size, np.float64)
+    intr, extr = _cam(intrinsics, extrinsic)
+    om._lib.om_tsdf_raycast(om._h, int(ell), int(value_bytes), intr.ctypes.data, extr.ctypes.data, int(width),
+                            ctypes.c_float(voxel), ctypes.c_float(depth_min), ctypes.c_float(step), int(n_steps),
+                            px.ctypes.data, px.size, out.ctypes.data)
     return out

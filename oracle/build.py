@@ -23,7 +23,10 @@ def build(mutant: int = 0, force: bool = False) -> str:
         return out
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-DORACLE_MUTANT={mutant}", SRC, "-o", tmp]
+    # -ffp-contract=off: float32 steps stay separately rounded on every host
+    # (Arm compilers contract a * b + c into a fused multiply-add otherwise).
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", f"-DORACLE_MUTANT={mutant}", SRC,
+           "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

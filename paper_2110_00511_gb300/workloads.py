@@ -11,6 +11,9 @@ Workload shapes:
     plus the three walls of a 10 m cube, Gaussian noise;
   * TSDF-shaped voxel-block keys from synthetic depth frames (Sec. 6.2):
     pinhole unprojection of smooth depth fields along a slow trajectory;
+  * depth frames of a static analytic room (walls + spheres) rendered along a
+    camera path, and the room's truncated signed distance sampled on voxel
+    blocks (inputs for TSDF integration and ray casting, Sec. 6.2);
   * a many-map batch and a Poisson serving trace.
 The paper's real scans are not available; these generators stand in for them.
 """
@@ -175,6 +178,100 @@ def tsdf_block_frames(n_frames: int = 200, seed: int = 0, voxel: float = 0.006, 
         pw = pc @ rot.T + pos
         keys = np.floor(pw / edge).astype(np.int32)
         yield np.ascontiguousarray(keys)
+
+
+@dataclass
+class RoomScene:
+    """A closed room [0, size]^3 with spheres (centre xyz, radius) inside."""
+    size: float
+    spheres: np.ndarray   # float64 [k, 4]
+
+
+def room_scene(seed: int = 0, size: float = 5.0, n_spheres: int = 12) -> RoomScene:
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.8, size - 0.8, size=(n_spheres, 3))
+    r = rng.uniform(0.15, 0.5, size=(n_spheres, 1))
+    return RoomScene(size=size, spheres=np.hstack([c, r]))
+
+
+def camera_path(n_frames: int, seed: int = 0, size: float = 5.0, orbit: float = 0.6, turn: float = 0.5):
+    """World-to-camera extrinsics [R | t] (float32 3x4) along a slow orbit
+    around the room's centre, turning through `turn` of a revolution."""
+    rng = np.random.default_rng(seed)
+    phase = rng.uniform(0, 2 * np.pi)
+    out = []
+    for f in range(n_frames):
+        a = f / max(1, n_frames)
+        pos = np.array([size / 2 + orbit * math.cos(2 * np.pi * a + phase),
+                        size / 2 + orbit * math.sin(2 * np.pi * a + phase), 1.5 + 0.1 * math.sin(4 * np.pi * a)])
+        r_cw = _rotation(2 * np.pi * turn * a + phase, 0.15 * math.sin(2 * np.pi * a))
+        r = r_cw.T
+        out.append(np.hstack([r, (-r @ pos)[:, None]]).astype(np.float32))
+    return out
+
+
+def render_depth(scene: RoomScene, extrinsic: np.ndarray, cam: Camera | None = None, noise: float = 0.0,
+                 seed: int = 0) -> np.ndarray:
+    """float32 [H, W] depth (distance along the optical axis) of the room seen
+    through a pinhole camera with world-to-camera `extrinsic`; Gaussian noise
+    of `noise` m if nonzero."""
+    cam = cam or Camera()
+    e = np.asarray(extrinsic, np.float64)
+    r, t = e[:, :3], e[:, 3]
+    pos = -r.T @ t
+    v, u = np.mgrid[0:cam.height, 0:cam.width]
+    dc = np.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, np.ones(u.shape)], -1).reshape(-1, 3)
+    dw = dc @ r                                   # camera -> world directions (camera z component 1)
+    best = np.full(dw.shape[0], np.inf)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for axis in range(3):
+            for wall in (0.0, scene.size):
+                tt = (wall - pos[axis]) / dw[:, axis]
+                best = np.where((tt > 0) & (tt < best), tt, best)
+    oc = pos[None, :] - scene.spheres[:, :3]      # [k, 3]
+    a = np.einsum("ij,ij->i", dw, dw)
+    for k in range(len(scene.spheres)):
+        b = 2 * dw @ oc[k]
+        cc = oc[k] @ oc[k] - scene.spheres[k, 3] ** 2
+        disc = b * b - 4 * a * cc
+        tt = np.where(disc > 0, (-b - np.sqrt(np.maximum(disc, 0))) / (2 * a), np.inf)
+        best = np.where((tt > 0) & (tt < best), tt, best)
+    depth = np.where(np.isfinite(best), best, 0.0)
+    if noise > 0:
+        depth = depth + np.random.default_rng(seed).normal(scale=noise, size=depth.shape)
+    return depth.reshape(cam.height, cam.width).astype(np.float32)
+
+
+def room_sdf(scene: RoomScene, x: np.ndarray) -> np.ndarray:
+    """Signed distance to the room's surfaces, positive in free space."""
+    d = np.minimum(np.min(x, axis=-1), np.min(scene.size - x, axis=-1))
+    for c in scene.spheres:
+        d = np.minimum(d, np.linalg.norm(x - c[:3], axis=-1) - c[3])
+    return d
+
+
+def block_lattice(keys: np.ndarray, voxel: float, ell: int = 8) -> np.ndarray:
+    """[n, ell^3, 3] world positions (K * ell + v) * voxel of the voxels of
+    blocks `keys`, voxel slot (vz * ell + vy) * ell + vx."""
+    g = np.stack(np.meshgrid(np.arange(ell), np.arange(ell), np.arange(ell), indexing="ij"), -1)
+    g = g.transpose(2, 1, 0, 3).reshape(-1, 3)
+    return (keys[:, None, :].astype(np.float64) * ell + g[None]) * voxel
+
+
+def room_tsdf_blocks(scene: RoomScene, voxel: float, trunc: float, ell: int = 8, band: int = 1):
+    """Voxel blocks within `band` blocks of a surface of the room and their
+    truncated signed distance clamp(sdf, -trunc, trunc) with weight 1
+    (float32 [n, ell^3] each), keys int32 [n, 3]."""
+    edge = voxel * ell
+    n = int(math.ceil(scene.size / edge))
+    k = np.stack(np.meshgrid(np.arange(-1, n + 1), np.arange(-1, n + 1), np.arange(-1, n + 1), indexing="ij"),
+                 -1).reshape(-1, 3)
+    centre = (k + 0.5) * edge
+    near = np.abs(room_sdf(scene, centre)) < (band + 0.87) * edge
+    keys = k[near].astype(np.int32)
+    x = block_lattice(keys, voxel, ell)
+    d = np.clip(room_sdf(scene, x), -trunc, trunc).astype(np.float32)
+    return np.ascontiguousarray(keys), np.ascontiguousarray(d), np.ones_like(d)
 
 
 def radius_offsets(r: int = 1, key_dim: int = 3) -> np.ndarray:
