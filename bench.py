@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--no-serving", action="store_true", help="skip the serving latency figures")
     p.add_argument("--serving-rates", type=str, default="2000,5000,10000,20000,50000")
     p.add_argument("--serving-requests", type=int, default=300)
+    p.add_argument("--no-tsdf", action="store_true", help="skip the voxel-block (TSDF) pipeline figures")
+    p.add_argument("--tsdf-frames", type=int, default=40)
     return p.parse_args(argv)
 
 
@@ -536,6 +538,13 @@ def main(argv=None):
     if not args.no_serving and not args.lean:
         serving = serving_figures(args, device)
 
+    tsdf = None
+    if not args.no_tsdf and not args.lean:
+        try:
+            tsdf = tsdf_figures(args, device, hbm_peak, rank == 0 and world == 1 and not args.no_cpu)
+        except Exception as e:  # noqa: BLE001
+            tsdf = {"error": str(e)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.lean:
         cpu = cpu_baseline(args, pts_np)
@@ -553,12 +562,130 @@ def main(argv=None):
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "kernels": kernels, "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "batched": batched, "serving": serving, "source_digest": source_digest()}
+                "ops": ops, "batched": batched, "serving": serving, "tsdf": tsdf, "source_digest": source_digest()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def bytes_integrate(n_blocks, n_updates, image_bytes):
+    """Per listed block: its index (4) and kB row (16); per updated voxel: d
+    and w read and written (16); the depth image read once (it stays in L2)."""
+    return n_blocks * 20 + n_updates * 16 + image_bytes
+
+
+def tsdf_figures(args, device, hbm_peak, with_cpu):
+    """The voxel-block pipeline of Sec. 6.2 on 640x480 depth frames of a
+    synthetic room: per frame depth -> block keys, the double hash map
+    (local map cleared per frame), TSDF integration of the frame's blocks,
+    and ray casting from the frame's pose through the local map.  6 mm voxels
+    in 8^3 blocks, truncation 4 voxels, depth in (0, 4] m."""
+    import torch
+    from paper_2110_00511_gb300 import ash, workloads
+    cam = workloads.Camera()
+    voxel, ell = 0.006, 8
+    trunc = 4 * voxel
+    depth_max, depth_min = 4.0, 0.3
+    step = voxel
+    n_steps = int((depth_max - depth_min) / step)
+    intr = (cam.fx, cam.fy, cam.cx, cam.cy)
+    scene = workloads.room_scene(0)
+    poses = workloads.camera_path(args.tsdf_frames, 0, turn=0.25)
+    depths = [torch.from_numpy(workloads.render_depth(scene, ex, cam, noise=0.002, seed=j)).to(device)
+              for j, ex in enumerate(poses)]
+    local = ash.HashMap(3, 1 << 17, [(1,)], [torch.int32], device=device)
+    vol = ash.HashMap(3, 1 << 19, [(ell, ell, ell), (ell, ell, ell)], [torch.float32, torch.float32], device=device)
+    out = torch.empty((cam.height, cam.width), dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def frame(j, trace_blocks):
+        keys = ash.ash_depth_to_block_keys(depths[j], intr, poses[j], voxel * ell, depth_max)
+        local.clear()
+        _, _, gi = ash.ash_double_map_activate(local, vol, keys)
+        ash.ash_tsdf_integrate(vol, gi, depths[j], intr, poses[j], voxel, trunc, depth_max)
+        ash.ash_tsdf_raycast(vol, intr, poses[j], cam.width, cam.height, voxel, depth_min, step, n_steps,
+                             local=local, out=out)
+        trace_blocks.append(gi.numel())
+
+    warm = []
+    for j in range(min(3, len(poses))):
+        frame(j, warm)
+    torch.cuda.synchronize()
+    # restart from an empty volume so the timed frames integrate the whole path
+    vol = ash.HashMap(3, 1 << 19, [(ell, ell, ell), (ell, ell, ell)], [torch.float32, torch.float32], device=device)
+    torch.cuda.synchronize()
+    ash.ash_trace_reset()
+    ash.ash_trace_enable(True)
+    blocks = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(len(poses)):
+        frame(j, blocks)
+    e1.record(stream)
+    ash.ash_trace_enable(False)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    trace = ash.ash_trace_collect()
+    n_updates = float(vol.value_buffer(1).sum().item())
+    kernels = {}
+    tot = sum(t for t, n in trace.values())
+    for name, (t, n) in trace.items():
+        if n:
+            kernels[name] = {"launches": n, "ms_per_launch": t / n, "share": t / tot if tot else 0.0}
+    integ_bytes = bytes_integrate(sum(blocks), n_updates, len(poses) * cam.width * cam.height * 4)
+    res = {"frames": len(poses), "image": [cam.width, cam.height], "voxel_m": voxel, "block": ell,
+           "trunc_m": trunc, "volume_blocks": vol.size(), "blocks_per_frame_mean": sum(blocks) / len(blocks),
+           "ms_per_frame": ms / len(poses), "frames_per_s": 1000.0 * len(poses) / ms,
+           "voxel_updates_per_frame": n_updates / len(poses), "kernels": kernels,
+           "timing": "CUDA events around all frames; each frame synchronises twice (key count, new-key count)"}
+    if "tsdf_integrate" in kernels:
+        ki = kernels["tsdf_integrate"]
+        gbs = integ_bytes / len(poses) / (ki["ms_per_launch"] / 1000.0) / 1e9
+        res["integrate"] = {"algo_bytes_per_frame": integ_bytes / len(poses), "achieved_gbs": gbs,
+                            "frac_hbm": gbs / hbm_peak,
+                            "voxels_per_s": sum(blocks) * ell ** 3 / (ki["ms_per_launch"] * len(poses) / 1000.0)}
+    if "tsdf_raycast" in kernels:
+        kr = kernels["tsdf_raycast"]
+        res["raycast"] = {"rays_per_s": cam.width * cam.height / (kr["ms_per_launch"] / 1000.0),
+                          "ns_per_ray": kr["ms_per_launch"] * 1e6 / (cam.width * cam.height),
+                          "max_samples_per_ray": n_steps, "through": "the frame's local map"}
+    # the double-hash-map speed-up of Sec. 6.2: the same ray casting through
+    # the whole volume's map and through the last frame's local map
+    def timed_rc(use_local, reps=5):
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ash.ash_tsdf_raycast(vol, intr, poses[-1], cam.width, cam.height, voxel, depth_min, step, n_steps,
+                                 local=local if use_local else None, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        return best
+    ms_global, ms_local = timed_rc(False), timed_rc(True)
+    res["raycast_global_vs_local"] = {"ms_global_map": ms_global, "ms_local_map": ms_local,
+                                      "speedup": ms_global / ms_local if ms_local else None}
+    if with_cpu:
+        import oracle
+        d = depths[0].cpu().numpy()
+        t0 = time.time()
+        okeys = oracle.depth_to_block_keys(d, intr, poses[0], voxel * ell, depth_max)
+        olocal = oracle.OracleMap(3, 1 << 17, [4])
+        ovol = oracle.OracleMap(3, 1 << 17, [8 * ell ** 3, 8 * ell ** 3])
+        _, _, ogi = oracle.double_map_activate(olocal, ovol, okeys)
+        oracle.tsdf_integrate(ovol, ogi, d, intr, poses[0], voxel, trunc, depth_max, ell=ell)
+        t_int = time.time() - t0
+        pix = np.arange(0, cam.width * cam.height, 97, dtype=np.int64)
+        t0 = time.time()
+        oracle.tsdf_raycast(ovol, intr, poses[0], cam.width, cam.height, voxel, depth_min, step, n_steps, pixels=pix,
+                            ell=ell, value_bytes=8)
+        t_rc = (time.time() - t0) * (cam.width * cam.height) / len(pix)
+        res["cpu_oracle"] = {"ms_per_frame": 1000.0 * (t_int + t_rc), "cores": 1,
+                             "sample": "frame 0: keys, double map and integration in full; ray casting on every "
+                                       "97th pixel, scaled to the image"}
+    return res
 
 
 def per_op_figures(args, device, hbm_peak):

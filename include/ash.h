@@ -386,6 +386,83 @@ uint64_t ash_kernel_launch_count(void);
 ash_status ash_probe_random_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed,
                                    uint32_t* sink, int64_t sink_len, ash_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Geometry consumers of the map (Sec. 6.2): the voxel-block pipeline of a
+ * volumetric reconstruction.  Cameras: intrinsics_host = {fx, fy, cx, cy};
+ * extrinsic_host = the world-to-camera pose [R | t], row-major 3x4 float32
+ * (the inverse of the frame pose T^j of Eq. (7)); both are host arrays read
+ * during the call.  Depth images are float32 [height, width] in device
+ * memory, in metres along the optical axis; a pixel has a measurement when
+ * 0 < D <= depth_max.  Every discrete decision (a block key, a pixel, a skip,
+ * a voxel, a zero crossing) is taken in float32 with explicitly rounded
+ * operations in the order given below, so any IEEE float32 implementation of
+ * the same steps reproduces it bit for bit.
+ * ------------------------------------------------------------------------- */
+
+/* Block keys of a depth frame (Sec. 6.2 unprojection, then Eq. (11)): pixel
+ * (px, py) with depth D gives the camera point
+ * x_c = [((px - cx) / fx) * D, ((py - cy) / fy) * D, D], the world point
+ * x_w = R^T x_c + c with c = -R^T t (each R^T row summed left to right), and
+ * the key floor(x_w / block_edge) per coordinate.  keys ([width * height, 3],
+ * device) receives the keys of the pixels with a measurement, in pixel order
+ * (row-major).  Their number goes to count_dev (a device int64, no host
+ * synchronisation) and/or count_host (synchronises the stream); at least one
+ * is required.  World coordinates must stay within |x_w / block_edge| < 2^31. */
+ash_status ash_depth_to_block_keys(const float* depth, int32_t width, int32_t height, const float* intrinsics_host,
+                                   const float* extrinsic_host, float block_edge, float depth_max, int32_t* keys,
+                                   int64_t* count_dev, int64_t* count_host, ash_stream stream);
+
+/* Double hash map block allocation (Sec. 6.2, the double-hash-map listing):
+ *   1. activate keys ([n, key_dim]) in `local`;
+ *   2. the keys whose activation succeeded (their first occurrences, in input
+ *      order) go to unique_keys [u, key_dim] with their local indices
+ *      local_indices [u];
+ *   3. activate them in `global`, then find them there: global_indices [u];
+ *   4. the local map's value buffer (one int32 element per entry) gets
+ *      local_v[local_indices[r]] = global_indices[r].
+ * The outputs need room for n rows; *n_unique_host = u.  Both maps grow by the
+ * usual rule.  Synchronises the stream once (to learn u before the global
+ * map's growth check).  The maps must be distinct, on one device, with the
+ * same key_dim; `local` must have exactly one value buffer of one int32. */
+ash_status ash_double_map_activate(ash_map* local, ash_map* global, const int32_t* keys, int64_t n,
+                                   int32_t* unique_keys, int32_t* local_indices, int32_t* global_indices,
+                                   int64_t* n_unique_host, ash_stream stream);
+
+/* TSDF integration of one depth frame (Sec. 6.2, Eq. (7)-(9)) into the voxel
+ * blocks at block_indices [n_blocks] (buffer indices of `blocks`, key_dim 3).
+ * Value buffers tsdf_buffer (signed distance d) and weight_buffer (weight w)
+ * are float32 rows of l^3 voxels, l = 8 or 16, voxel (vx, vy, vz) at slot
+ * (vz * l + vy) * l + vx.  For voxel g = K * l + v (K the block's key), the
+ * lattice point x = g * voxel_size goes to the camera, x_c = R x + t (rows
+ * ((r0 x + r1 y) + r2 z) + t); the voxel is left alone when z_c <= 0, when its
+ * pixel u = floor(fx * (x_c / z_c) + cx + 1/2), v = floor(fy * (y_c / z_c) +
+ * cy + 1/2) is outside the image, when D(u, v) has no measurement, or when
+ * d^j = D(u, v) - z_c < -trunc.  Otherwise, with Psi = min(d^j, trunc) and
+ * w^j = 1: d := (w * d + Psi) / (w + 1), w := w + 1 (Eq. (9)).  Indices outside
+ * [0, capacity) are skipped.  Block indices must be distinct within a call. */
+ash_status ash_tsdf_integrate(ash_map* blocks, int tsdf_buffer, int weight_buffer, const int32_t* block_indices,
+                              int64_t n_blocks, const float* depth, int32_t width, int32_t height,
+                              const float* intrinsics_host, const float* extrinsic_host, float voxel_size,
+                              float trunc, float depth_max, ash_stream stream);
+
+/* Ray casting (Sec. 6.2) into depth_out (float32 [height, width], device).
+ * The ray of pixel (px, py) leaves the camera centre c = -R^T t along
+ * dir = R^T [(px - cx) / fx, (py - cy) / fy, 1], so its parameter is the depth
+ * along the optical axis.  Sample i (0 <= i < n_steps) sits at
+ * t_i = depth_min + i * step, p = c + t_i * dir, and reads the nearest lattice
+ * point g = floor(p * r + 1/2), r = 1 / voxel_size in float32: block K = floor(g / l), voxel
+ * v = g - K * l.  It is valid when K is in the map and w > 0.  The first pair
+ * of consecutive valid samples with d_{i-1} > 0 >= d_i gives the depth
+ * t_{i-1} + step * d_{i-1} / (d_{i-1} - d_i); pixels without one get 0.
+ * local_index_map (optional): look blocks up in this map instead (key_dim 3,
+ * one int32 value per entry holding the block's index in `blocks`, same
+ * bucket size), as with the double hash map's local map; blocks it lacks
+ * read as empty.  n_steps <= 2^24. */
+ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer, const ash_map* local_index_map,
+                            const float* intrinsics_host, const float* extrinsic_host, int32_t width, int32_t height,
+                            float voxel_size, float depth_min, float step, int64_t n_steps, float* depth_out,
+                            ash_stream stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* ash_last_error(void);
 

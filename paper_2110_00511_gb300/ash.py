@@ -127,6 +127,13 @@ _SIGS = {
     "ash_server_stats_get": (_I32, [_P, ctypes.POINTER(ServerStats)]),
     "ash_server_map": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
     "ash_server_stream": (_I32, [_P, ctypes.POINTER(_P)]),
+    "ash_depth_to_block_keys": (_I32, [_P, _I32, _I32, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P,
+                                       ctypes.POINTER(_I64), _P]),
+    "ash_double_map_activate": (_I32, [_P, _P, _P, _I64, _P, _P, _P, ctypes.POINTER(_I64), _P]),
+    "ash_tsdf_integrate": (_I32, [_P, ctypes.c_int, ctypes.c_int, _P, _I64, _P, _I32, _I32, _P, _P, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, _P]),
+    "ash_tsdf_raycast": (_I32, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _I32, _I32, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, _I64, _P, _P]),
     "ash_last_error": (ctypes.c_char_p, []),
 }
 
@@ -690,3 +697,70 @@ class HashMap:
     @property
     def handle(self):
         return self._h
+
+
+# ------------------------------------------------------------ geometry (Sec. 6.2)
+def _cam_arrays(intrinsics, extrinsic):
+    intr = (ctypes.c_float * 4)(*[float(x) for x in intrinsics])
+    e = [float(x) for x in torch.as_tensor(extrinsic, dtype=torch.float32).reshape(12).tolist()]
+    return intr, (ctypes.c_float * 12)(*e)
+
+
+def ash_depth_to_block_keys(depth, intrinsics, extrinsic, block_edge, depth_max, keys=None, count_dev=None,
+                            sync=True, stream=None):
+    """Block keys of a float32 [H, W] depth image (pixel order, pixels with a
+    measurement only).  sync=True returns keys[:n]; otherwise (keys, count_dev)
+    with the count left in device memory."""
+    _need_cuda(depth, "depth", torch.float32)
+    h, w = depth.shape
+    if keys is None:
+        keys = torch.empty((h * w, 3), dtype=torch.int32, device=depth.device)
+    if count_dev is None and not sync:
+        count_dev = torch.zeros(1, dtype=torch.int64, device=depth.device)
+    intr, extr = _cam_arrays(intrinsics, extrinsic)
+    n = _I64(0)
+    _check(lib().ash_depth_to_block_keys(_ptr(depth), w, h, intr, extr, float(block_edge), float(depth_max),
+                                         _ptr(keys), _ptr(count_dev), ctypes.byref(n) if sync else None,
+                                         stream if stream is not None else _stream(depth.device)))
+    return keys[: n.value] if sync else (keys, count_dev)
+
+
+def ash_double_map_activate(local, glob, keys, stream=None):
+    """Double hash map block allocation (Sec. 6.2): returns (unique_keys [u, d],
+    local_indices [u], global_indices [u]); the local map's int32 values now
+    hold the global indices."""
+    keys = local._keys(keys)
+    n = keys.shape[0]
+    uk = torch.empty((n, local.key_dim), dtype=torch.int32, device=local.device)
+    li = torch.empty(n, dtype=torch.int32, device=local.device)
+    gi = torch.empty(n, dtype=torch.int32, device=local.device)
+    u = _I64(0)
+    _check(lib().ash_double_map_activate(local.handle, glob.handle, _ptr(keys), n, _ptr(uk), _ptr(li), _ptr(gi),
+                                         ctypes.byref(u), stream if stream is not None else _stream(local.device)))
+    return uk[: u.value], li[: u.value], gi[: u.value]
+
+
+def ash_tsdf_integrate(blocks, block_indices, depth, intrinsics, extrinsic, voxel_size, trunc, depth_max,
+                       tsdf_buffer=0, weight_buffer=1, stream=None):
+    """TSDF integration of one frame (Sec. 6.2, Eq. (7)-(9)) into the blocks at
+    block_indices (int32 device tensor of buffer indices)."""
+    _need_cuda(depth, "depth", torch.float32)
+    bi = block_indices.to(torch.int32).contiguous()
+    intr, extr = _cam_arrays(intrinsics, extrinsic)
+    h, w = depth.shape
+    _check(lib().ash_tsdf_integrate(blocks.handle, tsdf_buffer, weight_buffer, _ptr(bi), bi.numel(), _ptr(depth), w,
+                                    h, intr, extr, float(voxel_size), float(trunc), float(depth_max),
+                                    stream if stream is not None else _stream(blocks.device)))
+
+
+def ash_tsdf_raycast(blocks, intrinsics, extrinsic, width, height, voxel_size, depth_min, step, n_steps,
+                     local=None, tsdf_buffer=0, weight_buffer=1, out=None, stream=None):
+    """Ray-cast depth image (float32 [height, width]; 0 where no surface)."""
+    if out is None:
+        out = torch.empty((height, width), dtype=torch.float32, device=blocks.device)
+    intr, extr = _cam_arrays(intrinsics, extrinsic)
+    _check(lib().ash_tsdf_raycast(blocks.handle, tsdf_buffer, weight_buffer, local.handle if local is not None else None,
+                                  intr, extr, int(width), int(height), float(voxel_size), float(depth_min),
+                                  float(step), int(n_steps), _ptr(out),
+                                  stream if stream is not None else _stream(blocks.device)))
+    return out

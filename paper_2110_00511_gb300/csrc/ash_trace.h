@@ -24,6 +24,10 @@ enum KernelKind {
   kKSynthKeys,
   kKNeighbors,
   kKGatherValues,
+  kKDepthKeys,
+  kKCompact,
+  kKIntegrate,
+  kKRaycast,
   kKernelKinds
 };
 
