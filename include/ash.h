@@ -457,8 +457,12 @@ ash_status ash_tsdf_integrate(ash_map* blocks, int tsdf_buffer, int weight_buffe
  * local_index_map (optional): look blocks up in this map instead (key_dim 3,
  * one int32 value per entry holding the block's index in `blocks`, same
  * bucket size), as with the double hash map's local map; blocks it lacks
- * read as empty.  n_steps <= 2^24. */
-ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer, const ash_map* local_index_map,
+ * read as empty.  n_steps <= 2^24.  When depth_min > 0 the call first lists
+ * the lookup map's live blocks and projects them into per-tile depth ranges
+ * (the min-max estimate of Sec. 6.2), conservatively, so that rays skip
+ * only samples that no block can hold: the output is the same.  The maps are
+ * not modified (the listing uses their internal scratch). */
+ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer, ash_map* local_index_map,
                             const float* intrinsics_host, const float* extrinsic_host, int32_t width, int32_t height,
                             float voxel_size, float depth_min, float step, int64_t n_steps, float* depth_out,
                             ash_stream stream);

@@ -28,6 +28,7 @@ enum KernelKind {
   kKCompact,
   kKIntegrate,
   kKRaycast,
+  kKRayRange,
   kKernelKinds
 };
 

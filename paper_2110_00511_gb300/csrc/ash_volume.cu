@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(const int32_t* __re
     const float uf = floorf(__fadd_rn(__fadd_rn(__fmul_rn(cam.fx, __fdiv_rn(xc, zc)), cam.cx), 0.5f));
     const float vf = floorf(__fadd_rn(__fadd_rn(__fmul_rn(cam.fy, __fdiv_rn(yc, zc)), cam.cy), 0.5f));
     if (!(uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh)) continue;
-    const float dm = __ldg(depth + static_cast<int64_t>(vf) * width + static_cast<int64_t>(uf));
+    // uf, vf are in [0, 2^31): 32-bit conversions (64-bit ones run on the FP64 pipe)
+    const float dm = __ldg(depth + static_cast<int64_t>(static_cast<int32_t>(vf)) * width + static_cast<int32_t>(uf));
     if (!depth_valid(dm, depth_max)) continue;
     const float sdf = __fsub_rn(dm, zc);
     if (sdf < -trunc) continue;
@@ -230,6 +231,103 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(const int32_t* __re
     const float den = __fadd_rn(wv[q], 1.0f);
     trow[v] = __fdiv_rn(__fadd_rn(__fmul_rn(wv[q], dv[q]), psi), den);
     wrow[v] = den;
+  }
+}
+
+// ------------------------------------------------------ per-tile depth range
+// The min-max range estimate of Sec. 6.2: the live blocks of the map a ray
+// casting looks up are projected into tiles of kRangeTile x kRangeTile
+// pixels, each tile keeping the least and greatest camera depth any of those
+// blocks reaches over it.  A ray then samples only inside its tile's range.
+// The estimate is conservative, so the result is unchanged: a block's cell of
+// samples (the lattice points within half a voxel of it) is widened by half
+// a voxel more, its corners' pixel rectangle by one pixel, and a cell that
+// reaches the camera plane covers every tile from depth 0.  Samples outside
+// every listed cell read missing blocks, which are invalid.
+constexpr int kRangeTile = 8;
+
+__global__ void range_reset_kernel(unsigned int* __restrict__ zmin, unsigned int* __restrict__ zmax, int n_tiles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_tiles) {
+    zmin[i] = 0x7F800000u;  // +inf: no block over this tile yet
+    zmax[i] = 0u;
+  }
+}
+
+// Thread per live block (grid-stride over at most n_max entries of `live`,
+// the first *count_dev of which are valid).  Depths are positive, so their
+// float bit patterns order like the values and integer atomics keep the
+// extremes.
+__global__ void __launch_bounds__(kThreads) block_range_kernel(const int32_t* __restrict__ kb, int ks, int ell,
+                                                               const int32_t* __restrict__ live, int64_t n_max,
+                                                               const int64_t* __restrict__ count_dev, Cam cam,
+                                                               float voxel, int32_t width, int32_t height,
+                                                               int tiles_x, int tiles_y, unsigned int* __restrict__ zmin,
+                                                               unsigned int* __restrict__ zmax) {
+  int64_t n = *count_dev;
+  if (n > n_max) n = n_max;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t* key = kb + static_cast<int64_t>(__ldg(live + r)) * ks;
+    float lo[3], hi[3];
+    bool far_out = false;  // beyond |g| < 2^18 the margins are not proven: cover everything
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int32_t kk = __ldg(key + a);
+      far_out |= (kk >= (1 << 18) / ell || kk <= -(1 << 18) / ell);
+      const float k = static_cast<float>(kk) * static_cast<float>(ell);
+      lo[a] = (k - 1.0f) * voxel;
+      hi[a] = (k + static_cast<float>(ell)) * voxel;
+    }
+    float z_lo = 3.0e38f, z_hi = -3.0e38f, u_lo = 3.0e38f, u_hi = -3.0e38f, v_lo = 3.0e38f, v_hi = -3.0e38f;
+    bool behind = false;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+      const float x = (corner & 1) ? hi[0] : lo[0];
+      const float y = (corner & 2) ? hi[1] : lo[1];
+      const float z = (corner & 4) ? hi[2] : lo[2];
+      const float xc = cam.e[0] * x + cam.e[1] * y + cam.e[2] * z + cam.e[3];
+      const float yc = cam.e[4] * x + cam.e[5] * y + cam.e[6] * z + cam.e[7];
+      const float zc = cam.e[8] * x + cam.e[9] * y + cam.e[10] * z + cam.e[11];
+      z_lo = fminf(z_lo, zc);
+      z_hi = fmaxf(z_hi, zc);
+      if (zc <= 1.0e-6f) {
+        behind = true;
+      } else {
+        const float u = cam.fx * (xc / zc) + cam.cx;
+        const float v = cam.fy * (yc / zc) + cam.cy;
+        u_lo = fminf(u_lo, u);
+        u_hi = fmaxf(u_hi, u);
+        v_lo = fminf(v_lo, v);
+        v_hi = fmaxf(v_hi, v);
+      }
+    }
+    if (!far_out && !(z_hi > 0.0f)) continue;  // wholly behind the camera: no sample (t > 0) reaches it
+    int tx0, tx1, ty0, ty1;
+    unsigned int zl;
+    if (far_out) z_hi = __uint_as_float(0x7F800000u);
+    if (behind || far_out) {
+      tx0 = 0;
+      ty0 = 0;
+      tx1 = tiles_x - 1;
+      ty1 = tiles_y - 1;
+      zl = 0u;
+    } else {
+      const float px0 = fmaxf(floorf(u_lo) - 1.0f, 0.0f), px1 = fminf(ceilf(u_hi) + 1.0f, width - 1.0f);
+      const float py0 = fmaxf(floorf(v_lo) - 1.0f, 0.0f), py1 = fminf(ceilf(v_hi) + 1.0f, height - 1.0f);
+      if (!(px0 <= px1 && py0 <= py1)) continue;  // outside the image (or not finite)
+      tx0 = static_cast<int>(px0) / kRangeTile;
+      tx1 = static_cast<int>(px1) / kRangeTile;
+      ty0 = static_cast<int>(py0) / kRangeTile;
+      ty1 = static_cast<int>(py1) / kRangeTile;
+      zl = __float_as_uint(fmaxf(z_lo, 0.0f));
+    }
+    const unsigned int zh = __float_as_uint(z_hi);
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        atomicMin(zmin + ty * tiles_x + tx, zl);
+        atomicMax(zmax + ty * tiles_x + tx, zh);
+      }
   }
 }
 
@@ -257,11 +355,13 @@ struct RaySample {
   bool in_range;
 };
 
+// i < 2^24, so the conversion to float32 is exact (and int32 keeps it off the
+// 64-bit conversion path).
 __device__ __forceinline__ RaySample ray_sample(const float (&c)[3], const float (&dw)[3], float depth_min,
-                                                float step, float inv_voxel, int64_t i) {
+                                                float step, float inv_voxel, int32_t i) {
   RaySample r;
   r.in_range = true;
-  const float t = __fadd_rn(depth_min, __fmul_rn(static_cast<float>(i), step));
+  const float t = __fadd_rn(depth_min, __fmul_rn(__int2float_rn(i), step));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float gf = floorf(__fadd_rn(__fmul_rn(__fadd_rn(c[a], __fmul_rn(t, dw[a])), inv_voxel), 0.5f));
@@ -277,7 +377,7 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
                                           const float* __restrict__ tsdf, const float* __restrict__ weight,
                                           int32_t volume_capacity, const Cam& cam, int32_t width, int64_t pid,
                                           float voxel, float inv_voxel, float depth_min, float step, float inv_step,
-                                          int64_t n_steps) {
+                                          int32_t i_begin, int32_t n_steps) {
   constexpr int kVox = ELL * ELL * ELL;
   constexpr int kShift = ELL == 8 ? 3 : 4;
   const int32_t py = static_cast<int32_t>(pid / width);
@@ -299,8 +399,8 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
   bool prev_valid = false;
   float prev_d = 0.0f, prev_t = 0.0f;
   float out = 0.0f;
-  for (int64_t i = 0; i < n_steps; ++i) {
-    const float t = __fadd_rn(depth_min, __fmul_rn(static_cast<float>(i), step));
+  for (int32_t i = i_begin; i < n_steps; ++i) {
+    const float t = __fadd_rn(depth_min, __fmul_rn(__int2float_rn(i), step));
     const RaySample r = ray_sample(c, dw, depth_min, step, inv_voxel, i);
     bool valid = false;
     float dcur = 0.0f;
@@ -339,7 +439,7 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
         }
         const float est = floorf((t_exit - t) * inv_step);
         if (est >= 1.0f) {
-          int64_t m = i + static_cast<int64_t>(fminf(est, static_cast<float>(n_steps)));
+          int32_t m = i + static_cast<int32_t>(fminf(est, static_cast<float>(n_steps)));
           if (m > n_steps - 1) m = n_steps - 1;
           // confirm with the exact sample arithmetic; one step back if the
           // estimate crossed the face
@@ -366,7 +466,11 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
 }
 
 // Persistent grid; each warp takes the next 32 pixels from a counter, so rays
-// of uneven length do not leave the tail of the launch idle.
+// of uneven length do not leave the tail of the launch idle.  Each ray
+// samples only i in [i_begin, i_end) from its tile's depth range, widened by
+// two steps on either side; the sample before i_begin lies outside every
+// listed cell, so starting there with no valid predecessor is the same as
+// marching from 0.
 template <int ELL, int S>
 __global__ void __launch_bounds__(kThreads) raycast_kernel(TableView tv, TableView local_tv,
                                                            const int32_t* __restrict__ local_values, int use_local,
@@ -374,8 +478,10 @@ __global__ void __launch_bounds__(kThreads) raycast_kernel(TableView tv, TableVi
                                                            const float* __restrict__ weight, int32_t volume_capacity,
                                                            Cam cam, int32_t width, int64_t n_pixels, float voxel,
                                                            float inv_voxel, float depth_min, float step,
-                                                           float inv_step, int64_t n_steps,
-                                                           unsigned long long* __restrict__ next_chunk,
+                                                           float inv_step, int32_t n_steps,
+                                                           const unsigned int* __restrict__ zmin,
+                                                           const unsigned int* __restrict__ zmax, int tiles_x,
+                                                           int use_range, unsigned long long* __restrict__ next_chunk,
                                                            float* __restrict__ depth_out) {
   const int lane = threadIdx.x & 31;
   const uint64_t n_chunks = static_cast<uint64_t>((n_pixels + 31) / 32);
@@ -385,9 +491,31 @@ __global__ void __launch_bounds__(kThreads) raycast_kernel(TableView tv, TableVi
     chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
     if (chunk >= n_chunks) break;
     const int64_t pid = static_cast<int64_t>(chunk) * 32 + lane;
-    if (pid < n_pixels)
-      depth_out[pid] = cast_ray<ELL, S>(tv, local_tv, local_values, use_local, tsdf, weight, volume_capacity, cam,
-                                        width, pid, voxel, inv_voxel, depth_min, step, inv_step, n_steps);
+    if (pid < n_pixels) {
+      const int32_t py = static_cast<int32_t>(pid / width);
+      const int32_t px = static_cast<int32_t>(pid - static_cast<int64_t>(py) * width);
+      int32_t i0 = 0, i1 = n_steps;
+      if (use_range) {
+        const int tile = (py / kRangeTile) * tiles_x + px / kRangeTile;
+        const float z0 = __uint_as_float(__ldg(zmin + tile));
+        const float z1 = __uint_as_float(__ldg(zmax + tile));
+        if (z0 <= z1) {
+          const float f0 = floorf((z0 - depth_min) * inv_step) - 2.0f;
+          const float f1 = ceilf((z1 - depth_min) * inv_step) + 2.0f;
+          i0 = f0 <= 0.0f ? 0 : (f0 >= static_cast<float>(n_steps) ? n_steps : static_cast<int32_t>(f0));
+          i1 = f1 >= static_cast<float>(n_steps) ? n_steps : (f1 <= 0.0f ? 0 : static_cast<int32_t>(f1));
+        } else {
+          i1 = 0;  // no listed block over this tile
+        }
+      }
+      float out = 0.0f;
+      {
+        if (i0 < i1)
+          out = cast_ray<ELL, S>(tv, local_tv, local_values, use_local, tsdf, weight, volume_capacity, cam, width, pid,
+                                 voxel, inv_voxel, depth_min, step, inv_step, i0, i1);
+      }
+      depth_out[pid] = out;
+    }
   }
 }
 
@@ -586,7 +714,7 @@ ash_status ash_tsdf_integrate(ash_map* blocks, int tsdf_buffer, int weight_buffe
   return check_launch("tsdf_integrate");
 }
 
-ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer, const ash_map* local_index_map,
+ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer, ash_map* local_index_map,
                             const float* intrinsics_host, const float* extrinsic_host, int32_t width, int32_t height,
                             float voxel_size, float depth_min, float step, int64_t n_steps, float* depth_out,
                             ash_stream stream) {
@@ -621,9 +749,34 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
   const int use_local = local_index_map ? 1 : 0;
   const float inv_voxel = 1.0f / voxel_size;  // one IEEE division, the same on every host
   const float inv_step = 1.0f / step;
-  unsigned long long* counter = static_cast<unsigned long long*>(ash::vol::scratch_alloc(16, st));
-  if (!counter) return fail(ASH_ERR_OOM, "scratch allocation failed");
+  // scratch: chunk counter | live count | tile zmin | tile zmax | live indices
+  ash_map* lookup = local_index_map ? local_index_map : blocks;
+  const int tiles_x = (width + ash::vol::kRangeTile - 1) / ash::vol::kRangeTile;
+  const int tiles_y = (height + ash::vol::kRangeTile - 1) / ash::vol::kRangeTile;
+  const int n_tiles = tiles_x * tiles_y;
+  const size_t off_tiles = 16, off_live = off_tiles + ((8 * static_cast<size_t>(n_tiles) + 15) / 16) * 16;
+  char* scratch = static_cast<char*>(ash::vol::scratch_alloc(off_live + 4 * static_cast<size_t>(lookup->capacity), st));
+  if (!scratch) return fail(ASH_ERR_OOM, "scratch allocation failed");
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(scratch);
+  int64_t* live_count = reinterpret_cast<int64_t*>(scratch + 8);
+  unsigned int* zmin = reinterpret_cast<unsigned int*>(scratch + off_tiles);
+  unsigned int* zmax = zmin + n_tiles;
+  int32_t* live = reinterpret_cast<int32_t*>(scratch + off_live);
   cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  // the per-tile depth range (Sec. 6.2's min-max estimate) needs samples at t > 0
+  const int use_range = depth_min > 0.0f ? 1 : 0;
+  if (use_range) {
+    ash_status ls = ash_get_active_indices_async(lookup, live, lookup->capacity, live_count, stream);
+    if (ls != ASH_OK) {
+      cudaFreeAsync(scratch, st);
+      return ls;
+    }
+    ash::TraceScope tr(ash::kKRayRange, st, 2);
+    ash::vol::range_reset_kernel<<<(n_tiles + 255) / 256, 256, 0, st>>>(zmin, zmax, n_tiles);
+    ash::vol::block_range_kernel<<<grid_for(lookup->capacity, launch_of(lookup, st)), ash::vol::kThreads, 0, st>>>(
+        lookup->kb, lookup->ks, ell, live, lookup->capacity, live_count, cam, voxel_size, width, height, tiles_x,
+        tiles_y, zmin, zmax);
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   const int64_t warps_needed = (n_pix + 31) / 32;
@@ -642,8 +795,9 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
 #define ASH_RAYCAST(E, SB)                                                                                          \
   ash::vol::raycast_kernel<E, SB><<<grid, ash::vol::kThreads, 0, st>>>(tv, ltv, lvals, use_local, tsdf, weight, cap, \
                                                                        cam, width, n_pix, voxel_size, inv_voxel,     \
-                                                                       depth_min, step, inv_step, n_steps, counter,  \
-                                                                       depth_out)
+                                                                       depth_min, step, inv_step,                    \
+                                                                       static_cast<int32_t>(n_steps), zmin, zmax,   \
+                                                                       tiles_x, use_range, counter, depth_out)
   if (ell == 8) {
     if (blocks->S == 4) ASH_RAYCAST(8, 4);
     else if (blocks->S == 8) ASH_RAYCAST(8, 8);
@@ -655,7 +809,7 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
   }
 #undef ASH_RAYCAST
   const ash_status s = check_launch("tsdf_raycast");
-  cudaFreeAsync(counter, st);
+  cudaFreeAsync(scratch, st);
   return s;
 }
 
