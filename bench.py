@@ -745,6 +745,22 @@ def per_op_figures(args, device, hbm_peak):
     rec("insert", min(ms_ins), bytes_claim(n) + bytes_commit(n, n, n_unique, 4), n)
     rec("find_hit", timed(lambda: hm.find(keys)), bytes_find(n, 0), n)
     rec("find_miss", timed(lambda: hm.find(miss)), bytes_find(0, n), n)
+    # thread-per-key vs warp-cooperative probing, on 32 B and 128 B buckets
+    cmp = {}
+    for S in (4, 16):
+        tt = ash.default_tuning()
+        tt.slots_per_bucket = S
+        hp = ash.HashMap(3, n, device=device, tuning=tt)
+        hp.activate(keys)
+        for wp in (0, 1):
+            tt.warp_probe = wp
+            hp.set_tuning(tt)
+            name = f"S{S}_{'warp_group' if wp else 'thread_per_key'}"
+            ms_h = timed(lambda: hp.find(keys))
+            ms_m = timed(lambda: hp.find(miss))
+            cmp[name] = {"find_hit_ops_per_s": n / (ms_h / 1000), "find_miss_ops_per_s": n / (ms_m / 1000)}
+        del hp
+    out["probe_compare"] = cmp
     ms_act = []
     for _ in range(3):
         h2 = ash.HashMap(3, n, device=device)

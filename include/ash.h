@@ -78,6 +78,11 @@ typedef struct ash_tuning {
                                  kernel after the commit */
   int32_t keys_per_thread;    /* 1, 2 or 4 keys handled together by each thread of the find, claim
                                  and commit kernels (more independent memory requests in flight) */
+  int32_t warp_probe;         /* find: 0 = one thread per key (keys_per_thread keys each);
+                                 1 = warp-cooperative probing, a group of slots_per_bucket / 2 lanes
+                                 per key, each lane comparing two slots from one 16-byte load and
+                                 verifying its matches with a 128-bit kB load, the group agreeing
+                                 by warp ballot */
 } ash_tuning;
 
 /* Fills *out with the defaults. */
@@ -289,7 +294,8 @@ ash_status ash_batch_run(ash_batch* batch, const ash_batch_op* ops_host, int n_o
 
 /* Autotuner: times activate + find on synthetic keys of this shape (n =
  * min(capacity, 2^20) keys, uniqueness `rho` in (0, 1]) for candidate bucket
- * sizes, table slots per unit of capacity and keys per thread, and writes the
+ * sizes, table slots per unit of capacity, keys per thread and thread-per-key
+ * vs warp-cooperative probing, and writes the
  * fastest tuning to *out_host.  Results are cached per (device, key_dim,
  * capacity class, rho class).  Synchronises the stream. */
 ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int device, ash_stream stream,

@@ -191,6 +191,77 @@ __global__ void __launch_bounds__(256) find_kernel(TableView t, const int32_t* _
   }
 }
 
+// Warp-cooperative find: a group of G = S / 2 lanes takes one key, each lane
+// loading two slots (one 16-byte load; the group reads the whole bucket in one
+// coalesced request), so a warp has 32 / G keys in flight.  Fingerprint
+// matches are verified by the lane that holds them with one 128-bit kB load;
+// the group agrees through __ballot_sync and the result comes from the
+// lowest verified lane (__shfl_sync).  Probing continues while no lane saw an
+// EMPTY slot.  Groups of one warp proceed together (warp-wide ballots), a
+// finished group voting false.  The alternative to find_kernel's thread per
+// key; the tuning's warp_probe picks one.
+template <int D, int S>
+__global__ void __launch_bounds__(256) find_group_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+                                                         int32_t* __restrict__ idx, uint8_t* __restrict__ mask) {
+  constexpr int G = S / 2;
+  constexpr int KEYS_PER_WARP = 32 / G;
+  constexpr uint32_t kGroupBits = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % G;               // lane within the group
+  const int grp = lane / G;               // group within the warp
+  const uint32_t gshift = static_cast<uint32_t>(grp * G);
+  const int64_t warp_global = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp_global * KEYS_PER_WARP; base < n; base += n_warps * KEYS_PER_WARP) {
+    const int64_t pos = base + grp;
+    bool active = pos < n;
+    int32_t k[D];
+    if (active) {
+      load_input_key<D>(keys, pos, k);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) k[j] = 0;
+    }
+    const uint64_t h = hash_key<D>(k);
+    const uint32_t fp = fingerprint(h);
+    uint32_t b = home_bucket(h, t.n_buckets);
+    int32_t out = -1;
+    for (uint32_t probe = 0; probe < t.max_probes; ++probe) {
+      const bool live = active;
+      bool found = false, empty = false;
+      uint32_t my = kNoIndex;
+      if (live) {
+        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(t.slots + static_cast<size_t>(b) * S) + sub);
+        empty = (w.x == kEmpty) || (w.y == kEmpty);
+        const bool m0 = hi32(w.x) == fp && lo32(w.x) < kClaimBit;
+        const bool m1 = hi32(w.y) == fp && lo32(w.y) < kClaimBit;
+        if (m0 && kb_equal<D>(t.kb, lo32(w.x), k)) my = lo32(w.x);
+        else if (m1 && kb_equal<D>(t.kb, lo32(w.y), k)) my = lo32(w.y);
+        found = my != kNoIndex;
+      }
+      const uint32_t fb = (__ballot_sync(0xFFFFFFFFu, found) >> gshift) & kGroupBits;
+      const uint32_t eb = (__ballot_sync(0xFFFFFFFFu, empty) >> gshift) & kGroupBits;
+      const int src = fb ? static_cast<int>(gshift) + __ffs(fb) - 1 : lane;
+      const uint32_t hit = __shfl_sync(0xFFFFFFFFu, my, src);
+      if (live) {
+        if (fb) {
+          out = static_cast<int32_t>(hit);
+          active = false;
+        } else if (eb) {
+          active = false;
+        } else {
+          b = next_bucket(b, t.n_buckets);
+        }
+      }
+      if (!__any_sync(0xFFFFFFFFu, active)) break;
+    }
+    if (pos < n && sub == 0) {
+      idx[pos] = out;
+      mask[pos] = out >= 0 ? 1 : 0;
+    }
+  }
+}
+
 // ------------------------------------------------------------- insert: claim
 // Result codes written to buf_indices[p] by the claim kernel.
 constexpr int32_t kClaimExists = -2;  // key already committed
@@ -656,6 +727,7 @@ struct DimKernels {
   void (*neighbors)(int S, const TableView&, const int32_t*, int64_t, int, int64_t, int32_t*, uint8_t*, const Launch&);
   void (*offsets)(int S, const TableView&, const int32_t*, int64_t, const int32_t*, int64_t, int32_t*, uint8_t*,
                   const Launch&);
+  void (*find_group)(int S, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
 };
 
 template <int D>
@@ -760,10 +832,26 @@ struct DimLaunchers {
     else if (S == 8) offsets_s<8>(t, keys, n, off, n_off, idx, mask, L);
     else offsets_s<16>(t, keys, n, off, n_off, idx, mask, L);
   }
+  template <int S>
+  static void find_group_s(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                           const Launch& L) {
+    TraceScope ts(kKFind, L.stream);
+    constexpr int kKeysPerBlock = 256 / (S / 2);
+    int64_t g = (n + kKeysPerBlock - 1) / kKeysPerBlock;
+    if (g > L.grid_cap) g = L.grid_cap;
+    find_group_kernel<D, S><<<static_cast<int>(g < 1 ? 1 : g), 256, 0, L.stream>>>(t, keys, n, idx, mask);
+  }
+  static void find_group(int S, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                         const Launch& L) {
+    if (S == 4) find_group_s<4>(t, keys, n, idx, mask, L);
+    else if (S == 8) find_group_s<8>(t, keys, n, idx, mask, L);
+    else find_group_s<16>(t, keys, n, idx, mask, L);
+  }
   static DimKernels table() {
     DimKernels k;
     k.neighbors = &neighbors;
     k.offsets = &offsets;
+    k.find_group = &find_group;
     k.find = &find;
     k.claim = &claim;
     k.commit = &commit;

@@ -582,3 +582,32 @@ def test_find_offsets_tables(table):
     if table == "radius1":
         ri, rm = hm.find_neighbors(dev(q), 1)
         assert torch.equal(ri, gi) and torch.equal(rm, gm)
+
+
+@pytest.mark.parametrize("S", [4, 8, 16])
+@pytest.mark.parametrize("d", [1, 3, 5, 8])
+def test_warp_cooperative_find(d, S):
+    """Warp-cooperative probing (lane groups, ballots) returns exactly what
+    the thread-per-key find returns, and both equal the oracle, on hits,
+    misses, ragged n and a long probe chain (load close to the rebuild
+    threshold)."""
+    rng = np.random.default_rng(81 + d + S)
+    cap = 40_000
+    t = ash.default_tuning()
+    t.slots_per_bucket = S
+    t.slots_per_capacity = 1.2  # high load: probe chains cross buckets
+    hm = ash.HashMap(d, cap, tuning=t)
+    om = oracle.OracleMap(d, cap)
+    keys = rng.integers(-40, 40, size=(33_333, d)).astype(np.int32)
+    hm.activate(dev(keys))
+    om.activate(keys)
+    q = np.concatenate([keys[::3], rng.integers(-45, 45, size=(20_001, d)).astype(np.int32)])
+    oi, om_ = om.find(q)
+    t.warp_probe = 0
+    hm.set_tuning(t)
+    ti, tm = hm.find(dev(q))
+    t.warp_probe = 1
+    hm.set_tuning(t)
+    wi, wm = hm.find(dev(q))
+    assert torch.equal(ti, wi) and torch.equal(tm, wm)
+    assert_op_parity(hm, q, wi, wm, oi, om_, check_distinct=False)
