@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--serving-rates", type=str, default="2000,5000,10000,20000,50000")
     p.add_argument("--serving-requests", type=int, default=300)
     p.add_argument("--no-tsdf", action="store_true", help="skip the voxel-block (TSDF) pipeline figures")
+    p.add_argument("--no-blocks", action="store_true", help="skip the TSDF-shaped block-map figures")
+    p.add_argument("--block-frames", type=int, default=200)
     p.add_argument("--tsdf-frames", type=int, default=40)
     return p.parse_args(argv)
 
@@ -538,6 +540,13 @@ def main(argv=None):
     if not args.no_serving and not args.lean:
         serving = serving_figures(args, device)
 
+    blocks = None
+    if not args.no_blocks and not args.lean:
+        try:
+            blocks = tsdf_block_map_figures(args, device, hbm_peak)
+        except Exception as e:  # noqa: BLE001
+            blocks = {"error": str(e)[:300]}
+
     tsdf = None
     if not args.no_tsdf and not args.lean:
         try:
@@ -562,12 +571,75 @@ def main(argv=None):
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "kernels": kernels, "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "batched": batched, "serving": serving, "tsdf": tsdf, "source_digest": source_digest()}
+                "ops": ops, "batched": batched, "serving": serving, "tsdf_block_map": blocks, "tsdf": tsdf,
+                "source_digest": source_digest()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def tsdf_block_map_figures(args, device, hbm_peak):
+    """The TSDF-shaped voxel-block map: 640x480 frames of synthetic smooth
+    depth (6 mm voxels, 8^3 blocks, 48 mm block keys) along a slow path;
+    capacity 2^20 with tsdf float32[8,8,8] and weight float16[8,8,8] value
+    buffers.  Per frame the double hash map activates the frame's blocks
+    (local map cleared per frame, global activate + find); after all frames
+    the 27-neighbourhood of every active block is found.  Frame keys are on
+    the device before timing."""
+    import torch
+    from paper_2110_00511_gb300 import ash, workloads
+    frames = [torch.from_numpy(k).to(device) for k in workloads.tsdf_block_frames(n_frames=args.block_frames, seed=0)]
+    n_points = sum(k.shape[0] for k in frames)
+    stream = torch.cuda.current_stream(device)
+
+    def run(trace):
+        gmap = ash.HashMap(3, 1 << 20, [(8, 8, 8), (8, 8, 8)], [torch.float32, torch.float16], device=device)
+        local = ash.HashMap(3, 1 << 19, [(1,)], [torch.int32], device=device)
+        torch.cuda.synchronize()
+        if trace:
+            ash.ash_trace_reset()
+            ash.ash_trace_enable(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        n_unique = 0
+        for k in frames:
+            local.clear()
+            uk, _, _ = ash.ash_double_map_activate(local, gmap, k)
+            n_unique += uk.shape[0]
+        e1.record(stream)
+        act, cnt = gmap.active_indices_async()
+        keys = gmap.gather_keys_count(act, cnt)
+        n_blocks = int(cnt.item())
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record(stream)
+        idx, mask = gmap.find_neighbors(keys[:n_blocks], 1)
+        e2.record(stream)
+        if trace:
+            ash.ash_trace_enable(False)
+        torch.cuda.synchronize()
+        return (e0.elapsed_time(e1), e1b.elapsed_time(e2), n_unique, n_blocks, int(mask.sum().item()))
+
+    run(False)  # warm-up: code, pools
+    ms_frames, ms_nb, n_unique, n_blocks, n_hits = run(True)
+    trace = ash.ash_trace_collect()
+    kernels = {}
+    tot = sum(t for t, n in trace.values())
+    for name, (t, n) in trace.items():
+        if n:
+            kernels[name] = {"launches": n, "ms_per_launch": t / n, "share": t / tot if tot else 0.0}
+    frame_ops = n_points + 2 * n_unique  # local activate + global activate and find
+    nb = 27 * n_blocks
+    nb_bytes = bytes_find(n_hits, nb - n_hits) - nb * 4 * 3 + n_blocks * 4 * 3  # keys read once per block
+    return {"frames": len(frames), "points": n_points, "frame_unique_blocks": n_unique, "active_blocks": n_blocks,
+            "ms_per_frame": ms_frames / len(frames),
+            "frame_hash_ops_per_s": frame_ops / (ms_frames / 1000.0),
+            "neighbourhood": {"queries": nb, "hits": n_hits, "ms": ms_nb, "ops_per_s": nb / (ms_nb / 1000.0),
+                              "algo_gbs": nb_bytes / (ms_nb / 1000.0) / 1e9,
+                              "frac_hbm": nb_bytes / (ms_nb / 1000.0) / 1e9 / hbm_peak},
+            "kernels": kernels,
+            "timing": "CUDA events; each frame synchronises once (the global map's growth check)"}
 
 
 def bytes_integrate(n_blocks, n_updates, image_bytes):
