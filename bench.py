@@ -55,6 +55,9 @@ def parse_args(argv=None):
     p.add_argument("--serving-requests", type=int, default=300)
     p.add_argument("--no-tsdf", action="store_true", help="skip the voxel-block (TSDF) pipeline figures")
     p.add_argument("--no-blocks", action="store_true", help="skip the TSDF-shaped block-map figures")
+    p.add_argument("--no-sweep", action="store_true", help="skip the uniqueness sweep")
+    p.add_argument("--sweep-points", type=str, default="",
+                   help="override the sweep points, e.g. 20000000:0.5,1000000:1.0")
     p.add_argument("--block-frames", type=int, default=200)
     p.add_argument("--tsdf-frames", type=int, default=40)
     return p.parse_args(argv)
@@ -436,6 +439,16 @@ def main(argv=None):
                 "unit": "GB/s", "frac": dk["achieved_gbs"] / hbm_peak,
                 "traffic": measured_traffic(dominant)}
 
+    # the two hash operations of the step, each over all of its kernels
+    op_roofline = {}
+    for op, parts in (("insert", ("insert_claim", "insert_commit")), ("find", ("find",))):
+        if all(p_ in kernels and "algo_bytes_per_launch" in kernels[p_] for p_ in parts):
+            nbytes = sum(kernels[p_]["algo_bytes_per_launch"] for p_ in parts)
+            ms_op = sum(kernels[p_]["ms_per_launch"] for p_ in parts)
+            gbs = nbytes / (ms_op / 1000.0) / 1e9
+            op_roofline[op] = {"kernels": list(parts), "algo_bytes": nbytes, "ms": ms_op,
+                               "keys_per_s": N / (ms_op / 1000.0), "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+
     # ----------------------------------------------- random-access rooflines
     # Measured by the library's own probe kernels: random sector reads at the
     # step's table footprint (64 MB), at 512 MiB and at 8 GiB; random 64-bit
@@ -540,6 +553,14 @@ def main(argv=None):
     if not args.no_serving and not args.lean:
         serving = serving_figures(args, device)
 
+    sweep = None
+    if not args.no_sweep and not args.lean:
+        try:
+            rr = probe.get("read32_8GiB_GBps") if isinstance(probe, dict) else None
+            sweep = sweep_figures(args, device, hbm_peak, rr)
+        except Exception as e:  # noqa: BLE001
+            sweep = {"error": str(e)[:300]}
+
     blocks = None
     if not args.no_blocks and not args.lean:
         try:
@@ -569,15 +590,98 @@ def main(argv=None):
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks.summary(), "kernels": kernels, "random_access_roofline": probe,
+                "clocks": clocks.summary(), "kernels": kernels, "hash_op_roofline": op_roofline,
+                "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "batched": batched, "serving": serving, "tsdf_block_map": blocks, "tsdf": tsdf,
+                "ops": ops, "batched": batched, "serving": serving, "sweep": sweep, "tsdf_block_map": blocks, "tsdf": tsdf,
                 "source_digest": source_digest()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def device_uniform_keys(n, rho, seed, device):
+    """n int32x3 keys with round(rho n) distinct values, drawn on the device:
+    U distinct keys uniform in [-2^20, 2^20)^3 (collisions in a 2^63 space
+    are negligible and the map counts the real number), each appearing once,
+    the rest uniform picks among them, shuffled.  The shape of the sweep's
+    generator in workloads.uniform_keys, for sizes where host generation
+    would dominate the run."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = max(1, int(round(rho * n)))
+    distinct = torch.randint(-(1 << 20), 1 << 20, (u, 3), generator=g, device=device, dtype=torch.int32)
+    pick = torch.cat([torch.arange(u, device=device),
+                      torch.randint(0, u, (n - u,), generator=g, device=device)])
+    pick = pick[torch.randperm(n, generator=g, device=device)]
+    return distinct[pick].contiguous()
+
+
+def sweep_figures(args, device, hbm_peak, random_read_gbs):
+    """The uniqueness sweep of the voxelization setting (Sec. 5.1 / 6.1
+    shape): n uniform int32x3 keys at uniqueness rho, capacity n, activate
+    then find of the same keys, L2 flushed before each timed call.  Each
+    point reports ops/s, algorithmic GB/s, the fraction of the HBM copy peak
+    and of the random-access roofline (the 8 GiB random 32-byte read probe),
+    and its working set in multiples of L2."""
+    import torch
+    from paper_2110_00511_gb300 import ash
+    l2 = torch.cuda.get_device_properties(device).L2_cache_size
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    if args.sweep_points:
+        points = [(int(a), float(b)) for a, b in (p_.split(":") for p_ in args.sweep_points.split(","))]
+    else:
+        points = [(n, r) for n in (10_000, 100_000, 1_000_000, 10_000_000) for r in (0.1, 0.5, 1.0)]
+        points += [(20_000_000, 0.5), (100_000_000, 0.5)]
+    out = {"l2_bytes": l2, "random_access_roofline_gbs": random_read_gbs, "points": []}
+
+    def timed(fn, reps=3, make=None):
+        best = None
+        for _ in range(reps):
+            arg = make() if make else None
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(arg)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    for n, rho in points:
+        keys = device_uniform_keys(n, rho, seed=1000 + n % 997 + int(rho * 10), device=device)
+        holder = {}
+
+        def make():
+            holder["hm"] = ash.HashMap(3, n, device=device)
+            torch.cuda.synchronize()
+            return holder["hm"]
+
+        with torch.cuda.nvtx.range(f"sweep_{n}_{rho}"):  # lets a profiler select one point
+            ms_act = timed(lambda hm: hm.activate(keys), make=make)
+            hm = holder["hm"]
+            n_unique = hm.size()
+            ms_find = timed(lambda _: hm.find(keys))
+        t = hm.tuning()
+        slots = n * t.slots_per_capacity
+        working = int(slots * 8 + n * 16 + n * 12 + n * 5)   # table, kB, keys in, outputs
+        b_act = bytes_claim(n) + bytes_commit(n, n, n_unique, 0)
+        b_find = bytes_find(n, 0)
+        rec = {"n": n, "rho": rho, "unique": n_unique, "working_set_x_l2": working / l2}
+        for name, ms, nbytes in (("activate", ms_act, b_act), ("find", ms_find, b_find)):
+            gbs = nbytes / (ms / 1000.0) / 1e9
+            rec[name] = {"ms": ms, "keys_per_s": n / (ms / 1000.0), "algo_gbs": gbs, "frac_hbm": gbs / hbm_peak,
+                         "frac_random_access_roofline": gbs / random_read_gbs if random_read_gbs else None}
+        out["points"].append(rec)
+        del hm, keys
+        holder.clear()
+        torch.cuda.empty_cache()
+    return out
 
 
 def tsdf_block_map_figures(args, device, hbm_peak):
