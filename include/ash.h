@@ -20,7 +20,13 @@
  * Conventions for every call
  *   - Pointers are DEVICE pointers of the map's device unless the name ends in
  *     _host.  The caller owns every input and output array; the library owns
- *     the table, the heap and the key/value buffers.
+ *     the table, the heap and the key/value buffers.  Where the device can
+ *     access pageable host memory (ash_get_device_info: a coherent CPU-GPU
+ *     system), the key, value, index, mask and point arrays of the map calls,
+ *     ash_quantize and the gathers may instead be ordinary host memory: the
+ *     kernels read and write it in place, with no staging copy.  The call
+ *     returns before the kernels finish, so such host arrays must stay valid
+ *     and untouched until the stream has reached that point.
  *   - Keys are row-major int32 [n, key_dim] with no padding.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *     enqueue their kernels on it and return without waiting unless the
@@ -472,6 +478,18 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
                             const float* intrinsics_host, const float* extrinsic_host, int32_t width, int32_t height,
                             float voxel_size, float depth_min, float step, int64_t n_steps, float* depth_out,
                             ash_stream stream);
+
+/* Device facts the library and its callers use: SM count, L2 bytes, and
+ * whether kernels may read and write ordinary (pageable) host memory
+ * directly (cudaDevAttrPageableMemoryAccess; on coherent CPU-GPU systems the
+ * key and output arrays of the map calls may then be host pointers). */
+typedef struct ash_device_info {
+  int32_t sm_count;
+  int64_t l2_bytes;
+  int32_t pageable_memory_access;
+  int32_t pageable_uses_host_page_tables;
+} ash_device_info;
+ash_status ash_get_device_info(int device, ash_device_info* out_host);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char* ash_last_error(void);

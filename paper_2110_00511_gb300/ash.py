@@ -66,6 +66,14 @@ class ServerStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class DeviceInfo(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("l2_bytes", ctypes.c_int64), ("pageable_memory_access", ctypes.c_int32),
+                ("pageable_uses_host_page_tables", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BatchOp(ctypes.Structure):
     _fields_ = [("map", ctypes.c_void_p), ("op", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_int64),
@@ -134,6 +142,7 @@ _SIGS = {
                                   ctypes.c_float, ctypes.c_float, _P]),
     "ash_tsdf_raycast": (_I32, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _I32, _I32, ctypes.c_float,
                                 ctypes.c_float, ctypes.c_float, _I64, _P, _P]),
+    "ash_get_device_info": (_I32, [ctypes.c_int, ctypes.POINTER(DeviceInfo)]),
     "ash_last_error": (ctypes.c_char_p, []),
 }
 
@@ -764,3 +773,9 @@ def ash_tsdf_raycast(blocks, intrinsics, extrinsic, width, height, voxel_size, d
                                   float(step), int(n_steps), _ptr(out),
                                   stream if stream is not None else _stream(blocks.device)))
     return out
+
+
+def ash_get_device_info(device=0) -> dict:
+    info = DeviceInfo()
+    _check(lib().ash_get_device_info(int(device), ctypes.byref(info)))
+    return info.as_dict()

@@ -391,6 +391,8 @@ ash_status ash_batch_run(ash_batch* b, const ash_batch_op* ops, int n_ops, ash_s
       if (ph == kPhaseInsert) {
         o.map->size_ub += o.n;
         o.map->used_ub += o.n;
+        o.map->added_since_snap += o.n;
+        note_insert_stream(o.map, st);
       }
     }
     tb->ph[ph].count = k - tb->ph[ph].first;
@@ -405,6 +407,8 @@ ash_status ash_batch_run(ash_batch* b, const ash_batch_op* ops, int n_ops, ash_s
     TraceScope ts(kKBatch, st, 5);
     if (cudaGraphLaunch(sl.exec, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
   }
+  for (int i = 0; i < n_ops; ++i)
+    if (ops[i].op == ASH_OP_INSERT || ops[i].op == ASH_OP_ACTIVATE) maybe_snapshot(ops[i].map, st);
   if (cudaEventRecord(sl.done, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventRecord");
   sl.used = true;
   return ASH_OK;

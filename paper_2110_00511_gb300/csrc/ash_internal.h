@@ -47,6 +47,19 @@ struct ash_map {
   int64_t list_scratch_bytes = 0;
   int64_t size_ub = 0;  // upper bound of live entries since the last sync
   int64_t used_ub = 0;  // upper bound of used slots since the last sync
+  // Non-blocking snapshot of the control block: copied to snap_host after a
+  // batch (once the bounds pass half the limits), read when snap_event has
+  // completed, to tighten the bounds without synchronising.
+  ash::Ctrl* snap_host = nullptr;
+  cudaEvent_t snap_event = nullptr;
+  int snap_state = 0;              // 0 idle, 1 in flight, 2 in flight but stale
+  int64_t added_since_snap = 0;    // insert/activate keys issued after the snapshot's copy
+  // Snapshots are taken only while every insert/activate of the map has come
+  // on one stream (then stream order makes "snapshot + keys issued since" an
+  // upper bound); a second stream turns them off for the map's life.
+  cudaStream_t insert_stream = nullptr;
+  bool insert_streams_mixed = false;
+  bool any_insert = false;
   ash_tuning tuning{};
   ash::DimKernels K{};
   ash::host::Allocator alloc;
@@ -84,6 +97,14 @@ ash_status check_keys(const ash_map* m, const void* keys, int64_t n);
 ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st);
 // Growth to new_capacity >= capacity, enqueued on st with no host synchronisation.
 ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st);
+// Tightens size_ub / used_ub from a completed control-block snapshot (never blocks).
+void tighten_bounds(ash_map* m);
+// Marks an in-flight snapshot stale (after clear / rebuild change the count).
+void invalidate_snapshot(ash_map* m);
+// Enqueues a control-block snapshot on st once a bound passes half its limit.
+void maybe_snapshot(ash_map* m, cudaStream_t st);
+// Records the stream of an insert/activate (snapshots need a single one).
+void note_insert_stream(ash_map* m, cudaStream_t st);
 
 }  // namespace host
 }  // namespace ash

@@ -210,7 +210,58 @@ ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int
   if (status) *status = m->ctrl_host->status;
   m->size_ub = *top;
   m->used_ub = *used;
+  tighten_bounds(m);  // the stream is idle: a pending snapshot has landed
+  m->size_ub = *top;
+  m->used_ub = *used;
   return ASH_OK;
+}
+
+void tighten_bounds(ash_map* m) {
+  if (m->snap_state == 0 || cudaEventQuery(m->snap_event) != cudaSuccess) {
+    cudaGetLastError();  // cudaErrorNotReady is not an error here
+    return;
+  }
+  if (m->snap_state == 1) {
+    const unsigned long long tu = m->snap_host->top_used;
+    const int64_t top = static_cast<int64_t>(tu & 0xFFFFFFFFull) + m->added_since_snap;
+    const int64_t used = static_cast<int64_t>(tu >> 32) + m->added_since_snap;
+    if (top < m->size_ub) m->size_ub = top;
+    if (used < m->used_ub) m->used_ub = used;
+  }
+  m->snap_state = 0;
+}
+
+void invalidate_snapshot(ash_map* m) {
+  if (m->snap_state == 1) m->snap_state = 2;
+}
+
+// After a batch: once a bound passes half its limit, copy the control block
+// to the snapshot mirror (asynchronously) so that a later growth check can
+// tighten the bound without a synchronisation.
+void note_insert_stream(ash_map* m, cudaStream_t st) {
+  if (m->any_insert && m->insert_stream != st) m->insert_streams_mixed = true;
+  m->insert_stream = st;
+  m->any_insert = true;
+}
+
+void maybe_snapshot(ash_map* m, cudaStream_t st) {
+  if (m->snap_state != 0 || !m->snap_host || m->insert_streams_mixed || st != m->insert_stream) return;
+  const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
+  if (2 * m->size_ub <= m->capacity && 2 * m->used_ub <= max_used) return;
+  if (!m->snap_event) {
+    if (cudaEventCreateWithFlags(&m->snap_event, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      m->snap_event = nullptr;
+      return;
+    }
+  }
+  if (cudaMemcpyAsync(m->snap_host, m->ctrl, sizeof(ash::Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaEventRecord(m->snap_event, st) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  m->snap_state = 1;
+  m->added_since_snap = 0;
 }
 
 ash_status status_from_bits(int bits) {
@@ -384,6 +435,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
   dev_free(m, list, st);
   m->size_ub = size;
   m->used_ub = size;
+  invalidate_snapshot(m);
   return check_launch("rehash");
 }
 
@@ -472,6 +524,7 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
 // slots (live + tombstones) could pass max_used_fraction.
 ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st) {
   const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
+  if (m->size_ub + n > m->capacity || m->used_ub + n > max_used) tighten_bounds(m);
   const bool size_risk = m->size_ub + n > m->capacity;
   const bool used_risk = m->used_ub + n > max_used;
   if (!size_risk && !used_risk) return ASH_OK;
@@ -541,6 +594,9 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
   m->size_ub += n;
   m->used_ub += n;
+  m->added_since_snap += n;
+  note_insert_stream(m, st);
+  maybe_snapshot(m, st);
   return check_launch("insert");
 }
 
@@ -612,7 +668,10 @@ ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
   m->ctrl_host = pinned_ctrl_take();
-  if (!m->ctrl_host) {
+  m->snap_host = pinned_ctrl_take();
+  if (!m->ctrl_host || !m->snap_host) {
+    pinned_ctrl_give(m->ctrl_host);
+    pinned_ctrl_give(m->snap_host);
     delete m;
     return fail(ASH_ERR_OOM, "pinned host allocation failed");
   }
@@ -641,6 +700,14 @@ ash_status ash_destroy(ash_map* m) {
   dev_free(m, m->list_scratch, st);
   dev_free(m, m->ctrl, st);
   pinned_ctrl_give(m->ctrl_host);
+  if (m->snap_event) {
+    // a snapshot copy may still be landing in the pinned slot: let it finish
+    // before the slot goes back to the pool
+    if (m->snap_state != 0) cudaEventSynchronize(m->snap_event);
+    cudaEventDestroy(m->snap_event);
+    cudaGetLastError();
+  }
+  pinned_ctrl_give(m->snap_host);
   delete m;
   return ASH_OK;
 }
@@ -809,6 +876,7 @@ ash_status ash_clear(ash_map* m, ash_stream stream) {
   ash::launch_set_top_used(m->ctrl, 0, 0, L);
   m->size_ub = 0;
   m->used_ub = 0;
+  invalidate_snapshot(m);
   return check_launch("clear");
 }
 
@@ -968,6 +1036,24 @@ ash_status ash_probe_random_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, 
   L.grid_cap = sm_count(dev) * 8;
   ash::launch_probe_atomic(buf, buf_bytes, n_ops, mode, seed, sink, sink_len, L);
   return check_launch("probe_atomic");
+}
+
+ash_status ash_get_device_info(int device, ash_device_info* out) {
+  if (!out) return fail(ASH_ERR_INVALID, "out is NULL");
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return fail(ASH_ERR_INVALID, "no such CUDA device");
+  }
+  int v = 0;
+  out->sm_count = sm_count(device);
+  ASH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device));
+  out->l2_bytes = v;
+  ASH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, device));
+  out->pageable_memory_access = v;
+  ASH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device));
+  out->pageable_uses_host_page_tables = v;
+  return ASH_OK;
 }
 
 const char* ash_last_error(void) { return g_last_error.c_str(); }

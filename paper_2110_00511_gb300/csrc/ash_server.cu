@@ -118,6 +118,12 @@ struct ash_server {
   std::vector<ash_map*> maps;
   ash_batch* batch = nullptr;
   cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+  // Tenant growth runs on its own stream: only batches that include the
+  // growing tenant wait for it (grow_done[t]); the others keep running.
+  cudaStream_t s_grow = nullptr;
+  cudaEvent_t comp_mark = nullptr;
+  std::vector<cudaEvent_t> grow_done;
+  std::vector<char> growing;
   PinnedPool pinned;
   int64_t value_bytes = 0;
 
@@ -157,16 +163,25 @@ void CUDART_CB on_batch_done(void* arg) {
 
 // Worker-side: before an insert of n keys, grow the tenant map (x2 until it
 // fits) when the host's upper bound on its live entries would pass max_load
-// of the capacity.  The growth runs on the device, in stream order, with no
-// host synchronisation (grow_async), so it does not stall the pipeline.
-ash_status grow_for_insert(ash_server* s, ash_map* m, int64_t n) {
+// of the capacity.  The growth runs on the device with no host
+// synchronisation (grow_async), on the growth stream after the compute
+// stream's work so far (which may still read the old table); the tenant's
+// next batch waits for it, other tenants' batches do not.
+ash_status grow_for_insert(ash_server* s, int t, int64_t n) {
+  ash_map* m = s->maps[t];
   const double lim = s->cfg.max_load;
+  if (static_cast<double>(m->size_ub + n) > lim * static_cast<double>(m->capacity)) tighten_bounds(m);
   const double need = static_cast<double>(m->size_ub + n);
   if (need <= lim * static_cast<double>(m->capacity)) return ASH_OK;
   int64_t c = m->capacity;
   while (need > lim * static_cast<double>(c)) c *= 2;
-  ash_status st = grow_async(m, c, s->s_comp);
+  if (cudaEventRecord(s->comp_mark, s->s_comp) != cudaSuccess ||
+      cudaStreamWaitEvent(s->s_grow, s->comp_mark, 0) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "server growth ordering");
+  ash_status st = grow_async(m, c, s->s_grow);
   if (st != ASH_OK) return st;
+  if (cudaEventRecord(s->grow_done[t], s->s_grow) != cudaSuccess) return cuda_fail(cudaGetLastError(), "grow event");
+  s->growing[t] = 1;
   s->stats.rehashes += 1;
   return ASH_OK;
 }
@@ -218,7 +233,7 @@ void worker_loop(ash_server* s) {
     std::vector<ash_batch_op> ops;
     for (Request* r : pick) {
       if (r->op == ASH_OP_INSERT || r->op == ASH_OP_ACTIVATE) {
-        st = grow_for_insert(s, s->maps[r->tenant], r->n);
+        st = grow_for_insert(s, r->tenant, r->n);
         if (st != ASH_OK) break;
       }
     }
@@ -248,6 +263,12 @@ void worker_loop(ash_server* s) {
       cudaEventCreateWithFlags(&comp, cudaEventDisableTiming);
       cudaEventRecord(up, s->s_h2d);
       cudaStreamWaitEvent(s->s_comp, up, 0);
+      for (Request* r : pick) {
+        if (s->growing[r->tenant]) {
+          cudaStreamWaitEvent(s->s_comp, s->grow_done[r->tenant], 0);
+          s->growing[r->tenant] = 0;
+        }
+      }
       st = ash_batch_run(s->batch, ops.data(), static_cast<int>(ops.size()), reinterpret_cast<ash_stream>(s->s_comp));
       if (st == ASH_OK) {
         cudaEventRecord(comp, s->s_comp);
@@ -331,8 +352,15 @@ ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host
   DeviceGuard g(cfg->device);
   if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_grow, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->comp_mark, cudaEventDisableTiming) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "server streams");
+  s->grow_done.assign(cfg->n_tenants, nullptr);
+  s->growing.assign(cfg->n_tenants, 0);
+  for (int t = 0; t < cfg->n_tenants; ++t)
+    if (cudaEventCreateWithFlags(&s->grow_done[t], cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "server events");
   ash_status st = ash_batch_create(cfg->device, &s->batch);
   if (st != ASH_OK) return st;
   const int64_t numel = cfg->value_row_bytes / 4;
@@ -456,15 +484,19 @@ ash_status ash_server_destroy(ash_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   DeviceGuard g(s->cfg.device);
-  cudaStreamSynchronize(s->s_comp);
-  cudaStreamSynchronize(s->s_h2d);
-  cudaStreamSynchronize(s->s_d2h);
+  cudaStream_t all[4] = {s->s_comp, s->s_h2d, s->s_d2h, s->s_grow};
+  for (cudaStream_t x : all)
+    if (x) cudaStreamSynchronize(x);
   for (auto& kv : s->reqs) s->pinned.give(kv.second->host, kv.second->host_cls);
-  for (ash_map* m : s->maps) ash_destroy(m);
+  for (ash_map* m : s->maps) ash_destroy(m);  // frees on each map's last stream
+  for (cudaStream_t x : all)
+    if (x) cudaStreamSynchronize(x);
   ash_batch_destroy(s->batch);
-  cudaStreamDestroy(s->s_comp);
-  cudaStreamDestroy(s->s_h2d);
-  cudaStreamDestroy(s->s_d2h);
+  for (cudaEvent_t e : s->grow_done)
+    if (e) cudaEventDestroy(e);
+  if (s->comp_mark) cudaEventDestroy(s->comp_mark);
+  for (cudaStream_t x : all)
+    if (x) cudaStreamDestroy(x);
   delete s;
   return ASH_OK;
 }

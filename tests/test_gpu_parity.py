@@ -611,3 +611,38 @@ def test_warp_cooperative_find(d, S):
     wi, wm = hm.find(dev(q))
     assert torch.equal(ti, wi) and torch.equal(tm, wm)
     assert_op_parity(hm, q, wi, wm, oi, om_, check_distinct=False)
+
+
+@pytest.mark.parametrize("two_streams", [False, True])
+def test_repeated_batches_near_capacity(two_streams):
+    """Many insert / erase batches on one map that hovers near its capacity:
+    the host's bound on the live count is tightened from asynchronous
+    control-block snapshots (one stream) or by synchronising (two streams);
+    either way growth follows the oracle's rule exactly and the map equals
+    the oracle's."""
+    rng = np.random.default_rng(91 + two_streams)
+    pool = rng.integers(-10_000, 10_000, size=(9_000, 3)).astype(np.int32)
+    pool = np.unique(pool, axis=0)
+    hm = ash.HashMap(3, 10_000, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, 10_000, [4])
+    side = torch.cuda.Stream()
+    for r in range(120):
+        ins = pool[rng.integers(0, len(pool), size=700)]
+        vals = rng.random(700, dtype=np.float32)
+        if two_streams and r % 3 == 1:
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                gi, gm = hm.insert(dev(ins), [dev(vals)])
+            torch.cuda.current_stream().wait_stream(side)
+        else:
+            gi, gm = hm.insert(dev(ins), [dev(vals)])
+        oi, omask = om.insert(ins, [vals])
+        assert_op_parity(hm, ins, gi, gm, oi, omask)
+        er = pool[rng.integers(0, len(pool), size=350)]
+        assert np.array_equal(hm.erase(dev(er)).cpu().numpy(), om.erase(er))
+        if r % 20 == 19:
+            assert hm.capacity() == om.capacity()
+            assert_same_map(hm, om)
+    assert hm.capacity() == om.capacity()
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
