@@ -1135,7 +1135,8 @@ def serving_figures(args, device, n_tenants=16, clients=8):
     """Poisson arrivals over 16 resident tenant maps (int32x3 keys, one f32
     value), request sizes log-uniform in 1e3..1e6 keys, ops 30/60/10
     insert/find/erase.  Served form: the native continuous-batching server,
-    `clients` threads submitting at their scheduled arrival times.  Baseline:
+    `clients` threads submitting at their scheduled arrival times (staged,
+    and, where the device reads pageable host memory, zero-copy).  Baseline:
     the same requests as sequential plain calls (upload, op, download) in
     arrival order.  Latency = outputs on the host - scheduled arrival."""
     import threading
@@ -1165,9 +1166,13 @@ def serving_figures(args, device, n_tenants=16, clients=8):
 
     srv = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
                      device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256)
+    zc = ash.ash_get_device_info(device.index)["pageable_memory_access"] == 1
+    srv_zc = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
+                        device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
+                        zero_copy=1) if zc else None
     maps = [ash.HashMap(3, 1 << 20, [(1,)], [torch.float32], device=device) for _ in range(n_tenants)]
 
-    def run_served(arr, sizes, ops, tenants, starts):
+    def run_served(arr, sizes, ops, tenants, starts, srv=srv):
         lat = [0.0] * len(arr)
         rids = [None] * len(arr)
         t0 = time.perf_counter() + 0.02
@@ -1223,6 +1228,8 @@ def serving_figures(args, device, n_tenants=16, clients=8):
     # warm both forms (pinned staging classes, device pools, first growth) untimed
     warm = make_trace(1000.0, 99)
     run_served(*warm)
+    if srv_zc is not None:
+        run_served(*warm, srv=srv_zc)
     run_sequential(*warm)
     for ri, rate in enumerate(rates):
         trace = make_trace(rate, 100 + ri)
@@ -1234,11 +1241,23 @@ def serving_figures(args, device, n_tenants=16, clients=8):
         nb = st1["batches"] - st0["batches"]
         served["avg_requests_per_batch"] = (st1["batched_requests"] - st0["batched_requests"]) / max(1, nb)
         served["growth_rehashes"] = st1["rehashes"] - st0["rehashes"]
+        entry = {"served": served}
+        if srv_zc is not None:
+            z0 = srv_zc.stats()
+            zlat, zspan = run_served(*trace, srv=srv_zc)
+            z1 = srv_zc.stats()
+            zs = summarize(zlat, keys_total, zspan)
+            zb = z1["batches"] - z0["batches"]
+            zs["avg_requests_per_batch"] = (z1["batched_requests"] - z0["batched_requests"]) / max(1, zb)
+            zs["growth_rehashes"] = z1["rehashes"] - z0["rehashes"]
+            entry["served_zero_copy"] = zs
         seq_lat, seq_span = run_sequential(*trace)
-        seq = summarize(seq_lat, keys_total, seq_span)
-        out["rates"][str(int(rate))] = {"served": served, "sequential_plain": seq,
-                                        "offered_keys_per_s": keys_total / float(trace[0][-1])}
+        entry["sequential_plain"] = summarize(seq_lat, keys_total, seq_span)
+        entry["offered_keys_per_s"] = keys_total / float(trace[0][-1])
+        out["rates"][str(int(rate))] = entry
     srv.close()
+    if srv_zc is not None:
+        srv_zc.close()
     del maps
     return out
 

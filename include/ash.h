@@ -311,7 +311,8 @@ ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int device, as
  * Multi-tenant serving with continuous batching (no counterpart in the paper;
  * it serves the per-map operations above to many clients).  Tenant maps stay
  * resident.  ash_server_submit copies a request's keys (and values) from host
- * memory into pinned staging and queues it; a worker thread admits queued
+ * memory into pinned staging and queues it (with zero_copy the kernels use the
+ * caller's arrays in place instead); a worker thread admits queued
  * requests in arrival order while their device staging fits staging_bytes,
  * batches at most one request per tenant (so each tenant's requests apply in
  * arrival order), grows a tenant map x2 before an insert would push its
@@ -337,6 +338,12 @@ typedef struct ash_server_config {
   int64_t staging_bytes;      /* HBM budget for admitted requests' device buffers */
   float max_load;             /* grow before live/capacity would pass this (0.7) */
   int32_t max_batch_requests; /* requests per batch, 1..256 */
+  int32_t zero_copy;          /* 1: no staging.  The kernels read each request's keys and values from
+                                 the caller's host arrays and write buf_indices / masks into the
+                                 caller's arrays in place (devices with pageable memory access only,
+                                 see ash_get_device_info); all four arrays must stay valid and
+                                 unmodified from submit until wait returns.  Requests then take no
+                                 device staging and are admitted at once. */
 } ash_server_config;
 typedef struct ash_server_stats {
   int64_t submitted;

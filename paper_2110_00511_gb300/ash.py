@@ -55,7 +55,7 @@ ASH_OP_INSERT, ASH_OP_ACTIVATE, ASH_OP_FIND, ASH_OP_ERASE = range(4)
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_tenants", ctypes.c_int32), ("key_dim", ctypes.c_int32), ("initial_capacity", ctypes.c_int64),
                 ("value_row_bytes", ctypes.c_int32), ("device", ctypes.c_int32), ("staging_bytes", ctypes.c_int64),
-                ("max_load", ctypes.c_float), ("max_batch_requests", ctypes.c_int32)]
+                ("max_load", ctypes.c_float), ("max_batch_requests", ctypes.c_int32), ("zero_copy", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):

@@ -44,42 +44,88 @@ constexpr int kMaxTenants = 256;
 
 int64_t align256(int64_t x) { return (x + 255) & ~int64_t{255}; }
 
-// Pinned host blocks recycled by power-of-two size class.
+// Pinned host staging.  One pinned arena is allocated when the server is
+// created (pinning pages during serving is slow and stalls the caller), and
+// carved first-fit in 4 KiB units with coalescing frees.  When the arena is
+// full a block comes from cudaMallocHost and is cached by size for reuse.
 class PinnedPool {
  public:
+  void reserve(int64_t bytes) {
+    bytes = (bytes + kUnit - 1) / kUnit * kUnit;
+    if (bytes <= 0) return;
+    void* p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    base_ = static_cast<char*>(p);
+    size_ = bytes;
+    free_.emplace(0, bytes);
+  }
   void* take(int64_t bytes, int64_t* cls_bytes) {
-    int64_t c = 4096;
-    while (c < bytes) c <<= 1;
-    *cls_bytes = c;
+    const int64_t need = (bytes + kUnit - 1) / kUnit * kUnit;
     {
       std::lock_guard<std::mutex> lk(mu_);
-      auto& v = free_[c];
+      for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second < need) continue;
+        const int64_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > need) free_.emplace(off + need, len - need);
+        *cls_bytes = need;  // arena block: its size
+        return base_ + off;
+      }
+      auto& v = spill_[need];
       if (!v.empty()) {
         void* p = v.back();
         v.pop_back();
+        *cls_bytes = -need;  // spill block
         return p;
       }
     }
     void* p = nullptr;
-    if (cudaMallocHost(&p, c) != cudaSuccess) {
+    if (cudaMallocHost(&p, need) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
+    *cls_bytes = -need;
     return p;
   }
   void give(void* p, int64_t cls_bytes) {
     if (!p) return;
     std::lock_guard<std::mutex> lk(mu_);
-    free_[cls_bytes].push_back(p);
+    if (cls_bytes < 0) {
+      spill_[-cls_bytes].push_back(p);
+      return;
+    }
+    int64_t off = static_cast<char*>(p) - base_, len = cls_bytes;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + len == next->first) {  // merge with the following block
+      len += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {  // merge with the preceding block
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        off = prev->first;
+        len += prev->second;
+        free_.erase(prev);
+      }
+    }
+    free_.emplace(off, len);
   }
   ~PinnedPool() {
-    for (auto& kv : free_)
+    if (base_) cudaFreeHost(base_);
+    for (auto& kv : spill_)
       for (void* p : kv.second) cudaFreeHost(p);
   }
 
  private:
+  static constexpr int64_t kUnit = 4096;
   std::mutex mu_;
-  std::map<int64_t, std::vector<void*>> free_;
+  char* base_ = nullptr;
+  int64_t size_ = 0;
+  std::map<int64_t, int64_t> free_;                 // arena offset -> length
+  std::map<int64_t, std::vector<void*>> spill_;     // cudaMallocHost blocks by size
 };
 
 struct Request {
@@ -89,6 +135,9 @@ struct Request {
   int64_t n = 0;
   int32_t* idx_user = nullptr;
   uint8_t* mask_user = nullptr;
+  const int32_t* keys_user = nullptr;  // zero-copy: the caller's arrays, used in place
+  const void* vals_user = nullptr;
+  bool zero_copy = false;
   // staging: [keys | values | idx | mask], each 256-byte aligned
   int64_t off_keys = 0, off_vals = 0, off_idx = 0, off_mask = 0, bytes = 0;
   void* host = nullptr;
@@ -239,6 +288,18 @@ void worker_loop(ash_server* s) {
     }
     if (st == ASH_OK) {
       for (Request* r : pick) {
+        if (r->zero_copy) {
+          ash_batch_op o{};
+          o.map = s->maps[r->tenant];
+          o.op = r->op;
+          o.keys = r->keys_user;
+          o.values = (r->op == ASH_OP_INSERT && s->value_bytes > 0) ? r->vals_user : nullptr;
+          o.n = r->n;
+          o.buf_indices = r->idx_user;
+          o.masks = r->mask_user;
+          ops.push_back(o);
+          continue;
+        }
         if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, s->s_h2d) != cudaSuccess) {
           cudaGetLastError();
           st = ASH_ERR_OOM;
@@ -274,6 +335,7 @@ void worker_loop(ash_server* s) {
         cudaEventRecord(comp, s->s_comp);
         cudaStreamWaitEvent(s->s_d2h, comp, 0);
         for (Request* r : pick) {
+          if (r->zero_copy) continue;  // the kernels wrote the caller's arrays
           const int64_t out_bytes = r->bytes - r->off_idx;
           cudaMemcpyAsync(static_cast<char*>(r->host) + r->off_idx, r->dev + r->off_idx, out_bytes,
                           cudaMemcpyDeviceToHost, s->s_d2h);
@@ -285,7 +347,7 @@ void worker_loop(ash_server* s) {
         Batch* b = new Batch();
         b->reqs = pick;
         for (Request* r : pick) {
-          b->dev.push_back(r->dev);
+          if (r->dev) b->dev.push_back(r->dev);
           b->staged += r->bytes;
         }
         b->server = s;
@@ -334,6 +396,7 @@ void ash_server_default_config(ash_server_config* c) {
   c->staging_bytes = int64_t{2} << 30;
   c->max_load = 0.7f;
   c->max_batch_requests = 256;
+  c->zero_copy = 0;
 }
 
 ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host) {
@@ -346,9 +409,18 @@ ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host
   if (cfg->initial_capacity < 1 || cfg->staging_bytes < (1 << 20)) return fail(ASH_ERR_INVALID, "bad capacity or budget");
   if (!(cfg->max_load > 0.05f && cfg->max_load <= 1.0f)) return fail(ASH_ERR_INVALID, "max_load must be in (0.05, 1]");
   if (cfg->max_batch_requests < 1 || cfg->max_batch_requests > 256) return fail(ASH_ERR_INVALID, "max_batch_requests in 1..256");
+  if (cfg->zero_copy != 0 && cfg->zero_copy != 1) return fail(ASH_ERR_INVALID, "zero_copy must be 0 or 1");
+  if (cfg->zero_copy) {
+    ash_device_info info{};
+    ash_status ds = ash_get_device_info(cfg->device, &info);
+    if (ds != ASH_OK) return ds;
+    if (info.pageable_memory_access != 1)
+      return fail(ASH_ERR_INVALID, "zero_copy needs a device with pageable host memory access");
+  }
   std::unique_ptr<ash_server> s(new ash_server());
   s->cfg = *cfg;
   s->value_bytes = cfg->value_row_bytes;
+  if (!cfg->zero_copy) s->pinned.reserve(cfg->staging_bytes);  // host staging as large as the device budget
   DeviceGuard g(cfg->device);
   if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
@@ -401,6 +473,22 @@ ash_status ash_server_submit(ash_server* s, int32_t tenant, int32_t op, const in
   r->mask_user = masks_host;
   const int64_t kb = n * s->cfg.key_dim * 4;
   const int64_t vb = (op == ASH_OP_INSERT) ? n * s->value_bytes : 0;
+  if (s->cfg.zero_copy) {
+    r->zero_copy = true;
+    r->keys_user = keys_host;
+    r->vals_user = vb ? values_host : nullptr;
+    r->bytes = 0;  // no device staging
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return fail(ASH_ERR_INVALID, "server is stopping");
+    r->id = s->next_id++;
+    *request_id_host = r->id;
+    s->pending.push_back(r.get());
+    s->reqs.emplace(r->id, std::move(r));
+    s->stats.submitted += 1;
+    s->cv_work.notify_one();
+    return ASH_OK;
+  }
   r->off_keys = 0;
   r->off_vals = align256(kb);
   r->off_idx = r->off_vals + align256(vb);
@@ -446,9 +534,11 @@ ash_status ash_server_wait(ash_server* s, uint64_t request_id, int64_t timeout_m
     s->pinned.give(r->host, r->host_cls);
     return fail(werr, "the serving worker failed a batch: " + wmsg);
   }
-  if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, static_cast<char*>(r->host) + r->off_idx, r->n * 4);
-  std::memcpy(r->mask_user, static_cast<char*>(r->host) + r->off_mask, r->n);
-  s->pinned.give(r->host, r->host_cls);
+  if (!r->zero_copy) {
+    if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, static_cast<char*>(r->host) + r->off_idx, r->n * 4);
+    std::memcpy(r->mask_user, static_cast<char*>(r->host) + r->off_mask, r->n);
+    s->pinned.give(r->host, r->host_cls);
+  }
   if (latency_ms_host)
     *latency_ms_host = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   std::lock_guard<std::mutex> lk2(s->mu);

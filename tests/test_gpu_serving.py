@@ -65,11 +65,16 @@ def _check_same(reqs, served, alone, server_maps, alone_maps):
             assert (si[~sm] == -1).all()
 
 
-def test_served_results_equal_alone_and_oracle():
+@pytest.mark.parametrize("zero_copy", [0, 1])
+def test_served_results_equal_alone_and_oracle(zero_copy):
+    """Staged, and zero-copy (the kernels read the caller's arrays in place,
+    on devices with pageable host memory access)."""
+    if zero_copy and ash.ash_get_device_info(0)["pageable_memory_access"] != 1:
+        pytest.skip("no pageable memory access on this device")
     n_t = 4
     reqs = _trace(1, 80, n_t)
     srv = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=2048, value_row_bytes=4,
-                     staging_bytes=64 << 20, max_load=0.7, max_batch_requests=256)
+                     staging_bytes=64 << 20, max_load=0.7, max_batch_requests=256, zero_copy=zero_copy)
     ids = [srv.submit(t, OPS[op], keys, vals) for t, op, keys, vals in reqs]  # all in flight
     served = []
     for rid in ids:
@@ -114,6 +119,17 @@ def test_admission_under_a_small_budget():
     alone_maps, alone = _run_alone(reqs, n_t, 1 << 16)
     _check_same(reqs, served, alone, server_maps, alone_maps)
     srv.close()
+
+
+def test_zero_copy_refused_without_pageable_access():
+    if ash.ash_get_device_info(0)["pageable_memory_access"] == 1:
+        srv = ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=1)
+        srv.close()
+    else:
+        with pytest.raises(ash.AshError):
+            ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=1)
+    with pytest.raises(ash.AshError):
+        ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=2)
 
 
 def test_server_rejects_bad_requests():
