@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "hash ops/s (insert, find) & achieved HBM GB/s vs roofline; p50/p99 served latency"
 UNIT = "hash ops/s"
 L2_FLUSH_BYTES = 256 << 20
+TRACE_EVERY = 4
 WORKLOAD = ("point-cloud voxelization: 4M float32 points on 32 spheres + 3 planes in a 10 m cube "
             "(sigma 2 mm), 5 mm voxels, int32x3 keys, capacity = N")
 
@@ -416,9 +417,12 @@ def main(argv=None):
     launches0 = ash.ash_kernel_launch_count()
     t_wall0 = time.time()
     gc.disable()
-    ash.ash_trace_enable(True)
     for s in range(args.steps):
         flush.zero_()
+        # per-kernel events on every TRACE_EVERY-th timed step: the kernel
+        # durations come from the timed region without adding an event pair
+        # to every launch of every step
+        ash.ash_trace_enable(s % TRACE_EVERY == 0)
         starts[s].record(stream)
         _, uniq, count = step(pts, keys)
         ends[s].record(stream)
@@ -453,7 +457,8 @@ def main(argv=None):
     for name, (ms, n) in trace.items():
         if n == 0:
             continue
-        k = {"launches": n, "ms_per_launch": ms / n, "share": ms / total_kernel_ms if total_kernel_ms else 0.0}
+        k = {"traced_launches": n, "ms_per_launch": ms / n,
+             "share": ms / total_kernel_ms if total_kernel_ms else 0.0}
         if name in per_launch_bytes:
             gbs = per_launch_bytes[name] / (ms / n / 1000.0) / 1e9
             k.update({"algo_bytes_per_launch": per_launch_bytes[name], "achieved_gbs": gbs, "frac": gbs / hbm_peak})
@@ -626,6 +631,37 @@ def main(argv=None):
     except Exception as e:  # noqa: BLE001
         e2e = {"error": str(e)[:200]}
 
+    # ------------------------------------- the step replayed as a CUDA graph
+    graph_step = None
+    try:
+        if args.lean:
+            raise RuntimeError("skipped (--lean)")
+        cap = torch.cuda.Stream(device=device)
+        cap.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            _, _, g_count = step(pts, keys)
+        torch.cuda.synchronize()
+        gms = []
+        for s in range(min(args.steps, 200) + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            if s >= 3:
+                gms.append((e0, e1))
+        torch.cuda.synchronize()
+        gt = [a.elapsed_time(b) for a, b in gms]
+        graph_step = {"ms_median": statistics.median(gt), "ms_min": min(gt),
+                      "value": ops_per_step / (statistics.median(gt) / 1000.0), "unit": UNIT,
+                      "replays": len(gt), "unique_voxels": int(g_count.item()),
+                      "note": "the same step (map creation, quantize, insert, find, listing, gather, destroy) "
+                              "captured once and replayed; memory comes from graph allocation nodes"}
+        del g
+    except Exception as e:  # noqa: BLE001
+        graph_step = {"error": str(e)[:200]}
+
     # ------------------------------------------------- per-op figures (10^7)
     ops = None
     if not args.no_ops and not args.lean:
@@ -676,6 +712,7 @@ def main(argv=None):
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "graph_step": graph_step,
                 "clocks": clocks.summary(), "kernels": kernels, "hash_op_roofline": op_roofline,
                 "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},

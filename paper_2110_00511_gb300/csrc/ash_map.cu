@@ -246,6 +246,14 @@ void note_insert_stream(ash_map* m, cudaStream_t st) {
 
 void maybe_snapshot(ash_map* m, cudaStream_t st) {
   if (m->snap_state != 0 || !m->snap_host || m->insert_streams_mixed || st != m->insert_stream) return;
+  // Never inside a stream capture: a replayed graph would write the pinned
+  // slot long after this map (and its slot) are gone.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return;
   const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
   if (2 * m->size_ub <= m->capacity && 2 * m->used_ub <= max_used) return;
   if (!m->snap_event) {
