@@ -89,6 +89,9 @@ typedef struct ash_tuning {
                                  per key, each lane comparing two slots from one 16-byte load and
                                  verifying its matches with a 128-bit kB load, the group agreeing
                                  by warp ballot */
+  int32_t find_keys_per_thread; /* keys per thread of the thread-per-key find: 1, 2 or 4, or 0 to use
+                                   keys_per_thread (the find's dependent reads favour one key per
+                                   thread and full occupancy on mid-sized tables) */
 } ash_tuning;
 
 /* Fills *out with the defaults. */

@@ -189,6 +189,9 @@ ash_status validate_tuning(const ash_tuning& t) {
   if (t.keys_per_thread != 1 && t.keys_per_thread != 2 && t.keys_per_thread != 4)
     return fail(ASH_ERR_INVALID, "keys_per_thread must be 1, 2 or 4");
   if (t.warp_probe != 0 && t.warp_probe != 1) return fail(ASH_ERR_INVALID, "warp_probe must be 0 or 1");
+  if (t.find_keys_per_thread != 0 && t.find_keys_per_thread != 1 && t.find_keys_per_thread != 2 &&
+      t.find_keys_per_thread != 4)
+    return fail(ASH_ERR_INVALID, "find_keys_per_thread must be 0, 1, 2 or 4");
   return ASH_OK;
 }
 
@@ -627,6 +630,7 @@ void ash_default_tuning(ash_tuning* out) {
   out->inline_value_bytes = 16;
   out->keys_per_thread = 2;
   out->warp_probe = 0;
+  out->find_keys_per_thread = 1;
 }
 
 ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {
@@ -743,7 +747,8 @@ ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_ind
   if (m->tuning.warp_probe == 1)
     m->K.find_group(m->S, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
   else
-    m->K.find(m->S, m->tuning.keys_per_thread, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
+    m->K.find(m->S, m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread,
+              view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
   return check_launch("find");
 }
 

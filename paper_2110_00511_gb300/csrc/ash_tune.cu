@@ -81,18 +81,19 @@ extern "C" ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int
   ash_status status = ASH_OK;
   const int buckets[3] = {4, 8, 16};
   const float spcs[3] = {1.5f, 2.0f, 3.0f};
-  // keys per thread 1 and 2 with a thread per key, and warp-cooperative
-  // probing (which ignores keys_per_thread for the find)
-  const int kpts[3] = {1, 2, 0};
+  // (keys per thread, find keys per thread, warp-cooperative find):
+  // thread-per-key variants, and warp-cooperative probing
+  const int modes[4][3] = {{1, 1, 0}, {2, 1, 0}, {2, 2, 0}, {2, 1, 1}};
   for (int S : buckets) {
     for (float spc : spcs) {
-      for (int kpt : kpts) {
+      for (const auto& md : modes) {
         ash_tuning t;
         ash_default_tuning(&t);
         t.slots_per_bucket = S;
         t.slots_per_capacity = spc;
-        t.keys_per_thread = kpt == 0 ? 2 : kpt;
-        t.warp_probe = kpt == 0 ? 1 : 0;
+        t.keys_per_thread = md[0];
+        t.find_keys_per_thread = md[1];
+        t.warp_probe = md[2];
         float total = 0.0f;
         for (int rep = 0; rep < 2 && status == ASH_OK; ++rep) {
           ash_map* m = nullptr;

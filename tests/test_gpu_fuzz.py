@@ -37,6 +37,7 @@ def test_random_sequences(seed):
     t.slots_per_capacity = float(rng.choice([1.1, 1.5, 2.0, 4.0]))
     t.keys_per_thread = int(rng.choice([1, 2, 4]))
     t.warp_probe = int(rng.integers(0, 2))
+    t.find_keys_per_thread = int(rng.choice([0, 1, 2, 4]))
     t.block_threads = int(rng.choice([64, 128, 256]))
     vrow = int(rng.choice([0, 4, 12]))
     shapes, dtypes, rbs = ([], [], []) if vrow == 0 else ([(vrow // 4,)], [torch.float32], [vrow])
