@@ -375,6 +375,24 @@ def main(argv=None):
         del hm
         return fidx, uniq, count
 
+    def step_fused(points):
+        # The same step with the quantisation done inside the hash kernels
+        # (insert / find on the float32 points): no key array is written.
+        main = torch.cuda.current_stream(device)
+        aux.wait_stream(main)
+        with torch.cuda.stream(aux):
+            hm = ash.HashMap(3, N, [(1,)], [torch.int32], device=device)
+        main.wait_stream(aux)
+        hm.insert_points(points, args.voxel, [point_ids])
+        aux.wait_stream(main)
+        with torch.cuda.stream(aux):
+            act, count = hm.active_indices_async()
+            uniq = hm.gather_keys_count(act, count)
+        fidx, fmask = hm.find_points(points, args.voxel)
+        main.wait_stream(aux)
+        del hm
+        return fidx, uniq, count
+
     def step_zero_copy(host_pts, host_idx, host_mask, host_uniq, host_cnt):
         # The same step reading the points from host memory and writing the
         # per-point indices and masks, the unique voxel keys and their count to
@@ -662,6 +680,32 @@ def main(argv=None):
     except Exception as e:  # noqa: BLE001
         graph_step = {"error": str(e)[:200]}
 
+    # ------------------------------------ the step with in-kernel quantisation
+    fused = None
+    try:
+        if args.lean:
+            raise RuntimeError("skipped (--lean)")
+        for _ in range(3):
+            step_fused(pts)
+        torch.cuda.synchronize()
+        fev = []
+        for s in range(min(args.steps, 300)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, f_count = step_fused(pts)
+            e1.record(stream)
+            fev.append((e0, e1))
+        torch.cuda.synchronize()
+        ft = [a.elapsed_time(b) for a, b in fev]
+        fused = {"ms_median": statistics.median(ft), "ms_min": min(ft),
+                 "value": ops_per_step / (statistics.median(ft) / 1000.0), "unit": UNIT, "steps": len(ft),
+                 "unique_voxels": int(f_count.item()),
+                 "note": "insert and find take the float32 points and quantise them in the kernels "
+                         "(ash_insert_points / ash_find_points); outputs as the headline step"}
+    except Exception as e:  # noqa: BLE001
+        fused = {"error": str(e)[:200]}
+
     # ------------------------------------------------- per-op figures (10^7)
     ops = None
     if not args.no_ops and not args.lean:
@@ -712,7 +756,7 @@ def main(argv=None):
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "graph_step": graph_step,
+                "graph_step": graph_step, "fused_quantize_step": fused,
                 "clocks": clocks.summary(), "kernels": kernels, "hash_op_roofline": op_roofline,
                 "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},

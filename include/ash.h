@@ -155,6 +155,19 @@ ash_status ash_find(ash_map* map, const int32_t* keys, int64_t n, int32_t* buf_i
  *   masks: uint8 [n] out; 1 at the first position of each key that was
  *          stored, 0 elsewhere.
  * Uses n * 4 bytes of library-owned scratch (grown on demand). */
+/* The same operations on float32 points [n, key_dim]: each row's key is
+ * floor(p / cell) per coordinate, computed where the row is read, with an
+ * IEEE float32 division and rounding toward minus infinity (bit-identical to
+ * ash_quantize, the voxel key of Sec. 6.1).  Results, growth and errors are
+ * those of ash_insert / ash_activate / ash_find on the quantised keys; no key
+ * array is written.  cell > 0; the quantised keys must fit int32. */
+ash_status ash_insert_points(ash_map* map, const float* points, float cell, const void* const* values_host, int64_t n,
+                             int32_t* buf_indices, uint8_t* masks, ash_stream stream);
+ash_status ash_activate_points(ash_map* map, const float* points, float cell, int64_t n, int32_t* buf_indices,
+                               uint8_t* masks, ash_stream stream);
+ash_status ash_find_points(ash_map* map, const float* points, float cell, int64_t n, int32_t* buf_indices,
+                           uint8_t* masks, ash_stream stream);
+
 ash_status ash_erase(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
 
 /* Allocation-free erase.  The paper has no counterpart: this entry point

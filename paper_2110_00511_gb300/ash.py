@@ -110,6 +110,9 @@ _SIGS = {
     "ash_gather_keys": (_I32, [_P, _P, _I64, _P, _P]),
     "ash_gather_values": (_I32, [_P, ctypes.c_int, _P, _I64, _P, _P]),
     "ash_find_neighbors": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "ash_insert_points": (_I32, [_P, _P, ctypes.c_float, ctypes.POINTER(_P), _I64, _P, _P, _P]),
+    "ash_activate_points": (_I32, [_P, _P, ctypes.c_float, _I64, _P, _P, _P]),
+    "ash_find_points": (_I32, [_P, _P, ctypes.c_float, _I64, _P, _P, _P]),
     "ash_find_offsets": (_I32, [_P, _P, _I64, _P, _I64, _P, _P, _P]),
     "ash_get_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
@@ -632,6 +635,40 @@ class HashMap:
         out = torch.empty((idx.numel(), *self.value_shapes[j]), dtype=self.value_dtypes[j], device=self.device)
         _check(lib().ash_gather_values(self._h, j, _ptr(idx), idx.numel(), _ptr(out), _stream(self.device)))
         return out
+
+    def _points(self, points):
+        _need_cuda(points, "points", torch.float32)
+        if points.dim() != 2 or points.shape[1] != self.key_dim:
+            raise ValueError(f"points must be float32 [N, {self.key_dim}]")
+        return points
+
+    def insert_points(self, points, cell, values):
+        """insert() on the keys floor(points / cell), quantised in the kernels."""
+        points = self._points(points)
+        values = list(values) if isinstance(values, (list, tuple)) else [values]
+        if len(values) != len(self.value_shapes):
+            raise ValueError("one value tensor per value buffer is required")
+        for v, dt in zip(values, self.value_dtypes):
+            _need_cuda(v, "values", dt)
+        idx, mask = self._outputs(points.shape[0])
+        arr = (ctypes.c_void_p * max(1, len(values)))(*[v.data_ptr() for v in values])
+        _check(lib().ash_insert_points(self._h, _ptr(points), ctypes.c_float(cell), arr, points.shape[0], _ptr(idx),
+                                       _ptr(mask), _stream(self.device)))
+        return idx, mask
+
+    def activate_points(self, points, cell):
+        points = self._points(points)
+        idx, mask = self._outputs(points.shape[0])
+        _check(lib().ash_activate_points(self._h, _ptr(points), ctypes.c_float(cell), points.shape[0], _ptr(idx),
+                                         _ptr(mask), _stream(self.device)))
+        return idx, mask
+
+    def find_points(self, points, cell):
+        points = self._points(points)
+        idx, mask = self._outputs(points.shape[0])
+        _check(lib().ash_find_points(self._h, _ptr(points), ctypes.c_float(cell), points.shape[0], _ptr(idx),
+                                     _ptr(mask), _stream(self.device)))
+        return idx, mask
 
     def find_neighbors(self, keys, radius=1):
         """Masked queries of keys[r] + every offset in [-radius, radius]^d:

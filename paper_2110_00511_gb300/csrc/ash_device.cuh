@@ -134,9 +134,24 @@ __device__ __forceinline__ void load_input_key(const int32_t* __restrict__ keys,
   for (int j = 0; j < D; ++j) k[j] = __ldg(p + j);
 }
 
+// Input rows given as float32 points [n, D], quantised where they are read:
+// key = floor(p / cell) per coordinate with an IEEE float32 division and
+// rounding toward minus infinity (the voxel key of Sec. 6.1, bit-identical to
+// the quantisation kernel), so no key array is written or read.
+struct PointRows {
+  const float* p;
+  float cell;
+};
+
 template <int D>
-__device__ __forceinline__ bool input_key_equal(const int32_t* __restrict__ keys, int64_t pos,
-                                                const int32_t (&k)[D]) {
+__device__ __forceinline__ void load_input_key(const PointRows& in, int64_t pos, int32_t (&k)[D]) {
+  const float* q = in.p + pos * D;
+#pragma unroll
+  for (int j = 0; j < D; ++j) k[j] = __float2int_rd(__fdiv_rn(__ldg(q + j), in.cell));
+}
+
+template <int D, class In>
+__device__ __forceinline__ bool input_key_equal(const In& keys, int64_t pos, const int32_t (&k)[D]) {
   int32_t o[D];
   load_input_key<D>(keys, pos, o);
   bool eq = true;

@@ -62,8 +62,8 @@ __device__ __forceinline__ int32_t find_key(const TableView& t, const int32_t (&
 }
 
 // Scalar lookup of input row pos (the slow path of find).
-template <int D, int S>
-__device__ __noinline__ int32_t find_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
+template <int D, int S, class In>
+__device__ __noinline__ int32_t find_one(const TableView t, const In keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
   return find_key<D, S>(t, k);
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256) offsets_kernel(TableView t, const int32_t
 // KPT keys per thread: positions base, base + blockDim.x, ... so every load
 // instruction stays coalesced across the warp.  All home buckets are loaded
 // before any is examined, and all verify loads are issued before any compare.
-template <int D, int S, int KPT>
-__global__ void __launch_bounds__(256) find_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+template <int D, int S, int KPT, class In = const int32_t*>
+__global__ void __launch_bounds__(256) find_kernel(TableView t, const In keys, int64_t n,
                                                    int32_t* __restrict__ idx, uint8_t* __restrict__ mask) {
   constexpr int KS = KeyStride<D>::value;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) find_kernel(TableView t, const int32_t* _
         for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
         int32_t out = -1;
         if (eq) out = static_cast<int32_t>(cand[q]);
-        else if (ncand[q] > 0 || !stop[q]) out = find_one<D, S>(t, keys, pos);  // rare
+        else if (ncand[q] > 0 || !stop[q]) out = find_one<D, S, In>(t, keys, pos);  // rare
         idx[pos] = out;
         mask[pos] = out >= 0 ? 1 : 0;
       }
@@ -268,9 +268,9 @@ constexpr int32_t kClaimExists = -2;  // key already committed
 constexpr int32_t kClaimFailed = -1;  // no slot within max_probes
 
 // 0: no match.  1: slot claimed by an equal key in this batch.  2: committed equal key.
-template <int D>
-__device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_t (&k)[D],
-                                           const int32_t* __restrict__ keys, const int32_t* kb) {
+template <int D, class In>
+__device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_t (&k)[D], const In& keys,
+                                           const int32_t* kb) {
   const uint32_t lo = lo32(w);
   if (lo == kNoIndex || hi32(w) != fp) return 0;
   if (lo & kClaimBit) return input_key_equal<D>(keys, lo & ~kClaimBit, k) ? 1 : 0;
@@ -283,8 +283,8 @@ __device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_
 // 2) otherwise the EMPTY slots are claimed in order, and a lost CAS re-checks
 // the winner's word for an equal key; 3) a bucket without EMPTY slots sends
 // the key to the next bucket.
-template <int D, int S>
-__device__ __noinline__ int32_t claim_one(const TableView t, const int32_t* __restrict__ keys, int64_t pos) {
+template <int D, int S, class In>
+__device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
   const uint64_t h = hash_key<D>(k);
@@ -297,7 +297,7 @@ __device__ __noinline__ int32_t claim_one(const TableView t, const int32_t* __re
     load_bucket<S, false>(bp, w);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const int m = claim_match<D>(w[s], fp, k, keys, t.kb);
+      const int m = claim_match<D, In>(w[s], fp, k, keys, t.kb);
       if (m == 2) return kClaimExists;
       if (m == 1) {
         if ((lo32(w[s]) & ~kClaimBit) > static_cast<uint32_t>(pos))
@@ -312,7 +312,7 @@ __device__ __noinline__ int32_t claim_one(const TableView t, const int32_t* __re
                                        static_cast<unsigned long long>(kEmpty),
                                        static_cast<unsigned long long>(mine));
         if (old == kEmpty) return static_cast<int32_t>(b * S + s);
-        const int m = claim_match<D>(old, fp, k, keys, t.kb);
+        const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
         if (m == 2) return kClaimExists;
         if (m == 1) {
           if ((lo32(old) & ~kClaimBit) > static_cast<uint32_t>(pos))
@@ -333,8 +333,8 @@ __device__ __noinline__ int32_t claim_one(const TableView t, const int32_t* __re
 // The loads, compares and CASes of the KPT keys are issued back to back.
 // Anything else (several fingerprint matches, a lost CAS, a full bucket)
 // runs claim_one, which is safe because the fast path changed nothing then.
-template <int D, int S, int KPT>
-__global__ void __launch_bounds__(256) claim_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+template <int D, int S, int KPT, class In = const int32_t*>
+__global__ void __launch_bounds__(256) claim_kernel(TableView t, const In keys, int64_t n,
                                                     int32_t* __restrict__ slot_out) {
   constexpr int KS = KeyStride<D>::value;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) claim_kernel(TableView t, const int32_t* 
         if (old[q] == kEmpty) res[q] = static_cast<int32_t>(b[q] * S + es[q]);
         else slow[q] = true;
       }
-      if (slow[q]) res[q] = claim_one<D, S>(t, keys, pos);  // rare
+      if (slow[q]) res[q] = claim_one<D, S, In>(t, keys, pos);  // rare
       if (pos < n) slot_out[pos] = res[q];
     }
   }
@@ -472,8 +472,8 @@ __device__ __forceinline__ void copy_small_row(const ValueRow& v, int32_t i, int
 // block-wide scan ranks the winners and ONE heap atomic serves the iteration
 // (Sec. 4.3: t is raised by the number of indices taken).  Winners then write
 // kB(i), the value row, the committed slot word and their outputs.
-template <int D, int KPT, bool VAL>
-__device__ __forceinline__ void commit_tile(const TableView& t, const int32_t* __restrict__ keys, int64_t n,
+template <int D, int KPT, bool VAL, class In>
+__device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, int64_t n,
                                             int64_t base0, int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
                                             const ValueRow& v, int* s_warp, int* s_base, int* s_got) {
   const int64_t base = base0 + threadIdx.x;
@@ -546,8 +546,8 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const int32_t* _
   __syncthreads();
 }
 
-template <int D, int KPT, bool VAL>
-__global__ void __launch_bounds__(256) commit_kernel(TableView t, const int32_t* __restrict__ keys, int64_t n,
+template <int D, int KPT, bool VAL, class In = const int32_t*>
+__global__ void __launch_bounds__(256) commit_kernel(TableView t, const In keys, int64_t n,
                                                      int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
                                                      ValueRow v) {
   __shared__ int s_warp[33];
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256) commit_kernel(TableView t, const int32_t*
   __shared__ int s_got;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step)
-    commit_tile<D, KPT, VAL>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
+    commit_tile<D, KPT, VAL, In>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
 }
 
 // --------------------------------------------------------------- erase: mark
@@ -728,63 +728,96 @@ struct DimKernels {
   void (*offsets)(int S, const TableView&, const int32_t*, int64_t, const int32_t*, int64_t, int32_t*, uint8_t*,
                   const Launch&);
   void (*find_group)(int S, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
+  // the same operations on float32 points quantised in the kernels
+  void (*find_pts)(int S, int kpt, const TableView&, const PointRows&, int64_t, int32_t*, uint8_t*, const Launch&);
+  void (*claim_pts)(int S, int kpt, const TableView&, const PointRows&, int64_t, int32_t*, const Launch&);
+  void (*commit_pts)(int kpt, const TableView&, const PointRows&, int64_t, int32_t*, uint8_t*, const ValueRow*,
+                     const Launch&);
 };
 
 template <int D>
 struct DimLaunchers {
-  template <int S, int KPT>
-  static void find_sk(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
+  template <int S, int KPT, class In>
+  static void find_sk(const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
     TraceScope ts(kKFind, L.stream);
-    find_kernel<D, S, KPT><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask);
+    find_kernel<D, S, KPT, In><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask);
   }
-  template <int S>
-  static void find_s(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+  template <int S, class In>
+  static void find_s(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
                      const Launch& L) {
     if (kpt >= 4) find_sk<S, 4>(t, keys, n, idx, mask, L);
     else if (kpt == 2) find_sk<S, 2>(t, keys, n, idx, mask, L);
     else find_sk<S, 1>(t, keys, n, idx, mask, L);
   }
-  static void find(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
-                   const Launch& L) {
+  template <class In>
+  static void find_in(int S, int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
+                      const Launch& L) {
     if (S == 4) find_s<4>(kpt, t, keys, n, idx, mask, L);
     else if (S == 8) find_s<8>(kpt, t, keys, n, idx, mask, L);
     else find_s<16>(kpt, t, keys, n, idx, mask, L);
   }
-  template <int S, int KPT>
-  static void claim_sk(const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
-    TraceScope ts(kKClaim, L.stream);
-    claim_kernel<D, S, KPT><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+  static void find(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                   const Launch& L) {
+    find_in(S, kpt, t, keys, n, idx, mask, L);
   }
-  template <int S>
-  static void claim_s(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
+  static void find_pts(int S, int kpt, const TableView& t, const PointRows& p, int64_t n, int32_t* idx,
+                       uint8_t* mask, const Launch& L) {
+    find_in(S, kpt, t, p, n, idx, mask, L);
+  }
+  template <int S, int KPT, class In>
+  static void claim_sk(const TableView& t, const In& keys, int64_t n, int32_t* slot_out, const Launch& L) {
+    TraceScope ts(kKClaim, L.stream);
+    claim_kernel<D, S, KPT, In><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+  }
+  template <int S, class In>
+  static void claim_s(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* slot_out, const Launch& L) {
     if (kpt >= 4) claim_sk<S, 4>(t, keys, n, slot_out, L);
     else if (kpt == 2) claim_sk<S, 2>(t, keys, n, slot_out, L);
     else claim_sk<S, 1>(t, keys, n, slot_out, L);
   }
-  static void claim(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out,
-                    const Launch& L) {
+  template <class In>
+  static void claim_in(int S, int kpt, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,
+                       const Launch& L) {
     if (S == 4) claim_s<4>(kpt, t, keys, n, slot_out, L);
     else if (S == 8) claim_s<8>(kpt, t, keys, n, slot_out, L);
     else claim_s<16>(kpt, t, keys, n, slot_out, L);
   }
-  template <int KPT, bool VAL>
-  static void commit_kv(const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+  static void claim(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out,
+                    const Launch& L) {
+    claim_in(S, kpt, t, keys, n, slot_out, L);
+  }
+  static void claim_pts(int S, int kpt, const TableView& t, const PointRows& p, int64_t n, int32_t* slot_out,
+                        const Launch& L) {
+    claim_in(S, kpt, t, p, n, slot_out, L);
+  }
+  template <int KPT, bool VAL, class In>
+  static void commit_kv(const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
                         const ValueRow& v, const Launch& L) {
     TraceScope ts(kKCommit, L.stream);
-    commit_kernel<D, KPT, VAL><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
+    commit_kernel<D, KPT, VAL, In>
+        <<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
   }
-  template <bool VAL>
-  static void commit_v(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+  template <bool VAL, class In>
+  static void commit_v(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
                        const ValueRow& v, const Launch& L) {
     if (kpt >= 4) commit_kv<4, VAL>(t, keys, n, idx, mask, v, L);
     else if (kpt == 2) commit_kv<2, VAL>(t, keys, n, idx, mask, v, L);
     else commit_kv<1, VAL>(t, keys, n, idx, mask, v, L);
   }
   // v == nullptr: no inline value copy.
-  static void commit(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
-                     const ValueRow* v, const Launch& L) {
+  template <class In>
+  static void commit_in(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
+                        const ValueRow* v, const Launch& L) {
     if (v) commit_v<true>(kpt, t, keys, n, idx, mask, *v, L);
     else commit_v<false>(kpt, t, keys, n, idx, mask, ValueRow{}, L);
+  }
+  static void commit(int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* idx, uint8_t* mask,
+                     const ValueRow* v, const Launch& L) {
+    commit_in(kpt, t, keys, n, idx, mask, v, L);
+  }
+  static void commit_pts(int kpt, const TableView& t, const PointRows& p, int64_t n, int32_t* idx, uint8_t* mask,
+                         const ValueRow* v, const Launch& L) {
+    commit_in(kpt, t, p, n, idx, mask, v, L);
   }
   template <int S>
   static void erase_mark_s(const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out, const Launch& L) {
@@ -852,6 +885,9 @@ struct DimLaunchers {
     k.neighbors = &neighbors;
     k.offsets = &offsets;
     k.find_group = &find_group;
+    k.find_pts = &find_pts;
+    k.claim_pts = &claim_pts;
+    k.commit_pts = &commit_pts;
     k.find = &find;
     k.claim = &claim;
     k.commit = &commit;

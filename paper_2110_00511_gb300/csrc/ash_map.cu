@@ -559,8 +559,10 @@ ash_status check_keys(const ash_map* m, const void* keys, int64_t n) {
   return ASH_OK;
 }
 
+// pts != nullptr: the input rows are float32 points quantised in the kernels
+// (keys == pts->p then); otherwise int32 key rows.
 ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* values_host, int64_t n, int32_t* idx,
-                       uint8_t* mask, cudaStream_t st) {
+                       uint8_t* mask, cudaStream_t st, const ash::PointRows* pts = nullptr) {
   ash_status s = check_keys(m, keys, n);
   if (s != ASH_OK) return s;
   if (n == 0) return ASH_OK;
@@ -576,7 +578,8 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   const ash::Launch L = launch_of(m, st);
   const ash::TableView tv = view_of(m);
   const int kpt = m->tuning.keys_per_thread;
-  m->K.claim(m->S, kpt, tv, keys, n, idx, L);
+  if (pts) m->K.claim_pts(m->S, kpt, tv, *pts, n, idx, L);
+  else m->K.claim(m->S, kpt, tv, keys, n, idx, L);
   // one value buffer with small rows: copied by the committing thread;
   // anything else: warp-per-row scatter after the commit
   bool inline_value = false;
@@ -601,7 +604,8 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
       }
     }
   }
-  m->K.commit(kpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+  if (pts) m->K.commit_pts(kpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
+  else m->K.commit(kpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
   if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
   m->size_ub += n;
   m->used_ub += n;
@@ -750,6 +754,38 @@ ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_ind
     m->K.find(m->S, m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread,
               view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
   return check_launch("find");
+}
+
+ash_status ash_insert_points(ash_map* m, const float* points, float cell, const void* const* values_host, int64_t n,
+                             int32_t* buf_indices, uint8_t* masks, ash_stream stream) {
+  if (m && m->n_values > 0 && n > 0 && !values_host) return fail(ASH_ERR_INVALID, "values are required for insert");
+  if (!(cell > 0.0f)) return fail(ASH_ERR_INVALID, "cell must be > 0");
+  const ash::PointRows p{points, cell};
+  return insert_impl(m, reinterpret_cast<const int32_t*>(points), values_host, n, buf_indices, masks,
+                     reinterpret_cast<cudaStream_t>(stream), &p);
+}
+
+ash_status ash_activate_points(ash_map* m, const float* points, float cell, int64_t n, int32_t* buf_indices,
+                               uint8_t* masks, ash_stream stream) {
+  if (!(cell > 0.0f)) return fail(ASH_ERR_INVALID, "cell must be > 0");
+  const ash::PointRows p{points, cell};
+  return insert_impl(m, reinterpret_cast<const int32_t*>(points), nullptr, n, buf_indices, masks,
+                     reinterpret_cast<cudaStream_t>(stream), &p);
+}
+
+ash_status ash_find_points(ash_map* m, const float* points, float cell, int64_t n, int32_t* buf_indices,
+                           uint8_t* masks, ash_stream stream) {
+  ash_status s = check_keys(m, points, n);
+  if (s != ASH_OK) return s;
+  if (!(cell > 0.0f)) return fail(ASH_ERR_INVALID, "cell must be > 0");
+  if (n == 0) return ASH_OK;
+  if (!buf_indices || !masks) return fail(ASH_ERR_INVALID, "buf_indices and masks are required");
+  DeviceGuard g(m->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  m->last_stream = st;
+  const int kpt = m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread;
+  m->K.find_pts(m->S, kpt, view_of(m), ash::PointRows{points, cell}, n, buf_indices, masks, launch_of(m, st));
+  return check_launch("find_points");
 }
 
 ash_status ash_erase(ash_map* m, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream) {

@@ -646,3 +646,35 @@ def test_repeated_batches_near_capacity(two_streams):
     assert hm.capacity() == om.capacity()
     assert_same_map(hm, om)
     assert_heap_permutation(hm)
+
+
+@pytest.mark.parametrize("d,cell", [(3, 0.005), (3, 0.048), (2, 0.01), (1, 0.25)])
+def test_point_input_ops(d, cell):
+    """insert / activate / find on float32 points quantised in the kernels
+    equal the same operations on ash_quantize's keys, and the oracle
+    (quantisation of Sec. 6.1 + the map operations)."""
+    rng = np.random.default_rng(97 + d)
+    pts3 = workloads.voxel_scene_points(150_001, seed=d)
+    pts = np.ascontiguousarray(pts3[:, :d]) if d < 3 else pts3
+    pts = pts * np.float32(-1.0 if d == 2 else 1.0)  # negative coordinates too
+    keys = oracle.quantize(pts, cell)
+    ids = np.arange(len(pts), dtype=np.int32)
+    hm = ash.HashMap(d, len(pts) // 3, [(1,)], [torch.int32])   # grows
+    om = oracle.OracleMap(d, len(pts) // 3, [4])
+    gi, gm = hm.insert_points(dev(pts), cell, [dev(ids)])
+    oi, omask = om.insert(keys, [ids])
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert hm.capacity() == om.capacity()
+    q = np.concatenate([pts[::2], (pts[:5000] + np.float32(1000.0))])
+    fi, fm = hm.find_points(dev(q), cell)
+    ofi, ofm = om.find(oracle.quantize(q, cell))
+    assert_op_parity(hm, oracle.quantize(q, cell), fi, fm, ofi, ofm, check_distinct=False)
+    ki, km = hm.find(ash.ash_quantize(dev(q), cell))
+    assert torch.equal(ki, fi) and torch.equal(km, fm)
+    assert_same_map(hm, om)
+    hs = ash.HashMap(d, 1000)
+    ai, am = hs.activate_points(dev(pts), cell)
+    os_ = oracle.OracleMap(d, 1000)
+    aoi, aom = os_.activate(keys)
+    assert_op_parity(hs, keys, ai, am, aoi, aom)
+    assert_same_map(hs, os_)
