@@ -88,14 +88,19 @@ __device__ __forceinline__ int op_of_tile(const int64_t* s_tile0, int count, int
     default: FN<4, 16>(__VA_ARGS__); break;                         \
   }
 
+// In the batched kernels the full per-key protocols are the main path, so
+// they are inlined (the single-map kernels keep them out of line as their
+// rare slow path).
 template <int D, int S>
 __device__ __forceinline__ void batch_claim_one(const BatchOp& op, int64_t pos) {
-  op.idx[pos] = claim_one<D, S>(op.t, op.keys, pos);
+  op.idx[pos] = claim_key<D, S>(op.t, op.keys, pos);
 }
 
 template <int D, int S>
 __device__ __forceinline__ void batch_find_one(const BatchOp& op, int64_t pos) {
-  const int32_t r = find_one<D, S>(op.t, op.keys, pos);
+  int32_t k[D];
+  load_input_key<D>(op.keys, pos, k);
+  const int32_t r = find_key<D, S>(op.t, k);
   op.idx[pos] = r;
   op.mask[pos] = r >= 0 ? 1 : 0;
 }

@@ -284,7 +284,7 @@ __device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_
 // the winner's word for an equal key; 3) a bucket without EMPTY slots sends
 // the key to the next bucket.
 template <int D, int S, class In>
-__device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int64_t pos) {
+__device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
   const uint64_t h = hash_key<D>(k);
@@ -325,6 +325,13 @@ __device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int6
   }
   atomicOr(&t.ctrl->status, kStatusTableFull);
   return kClaimFailed;
+}
+
+// Out-of-line copy of the full protocol: the rare slow path of claim_kernel
+// (kept out of line so it does not raise the fast path's register count).
+template <int D, int S, class In>
+__device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int64_t pos) {
+  return claim_key<D, S, In>(t, keys, pos);
 }
 
 // KPT keys per thread.  Fast path per key, on its home bucket only: if the
