@@ -321,6 +321,30 @@ def cpu_baseline(args, pts_np):
                       f"single-threaded C++ oracle, {el:.1f} s"}
 
 
+def cpu_baseline_tsdf_frame(c):
+    """The CPU oracle on one frame of the voxel-block pipeline (the bench's
+    `tsdf` block): block keys, double hash map and integration in full, ray
+    casting on every 97th pixel scaled to the image, single-threaded."""
+    import oracle
+    cam = c["cam"]
+    t0 = time.perf_counter()
+    okeys = oracle.depth_to_block_keys(c["depth"], c["intr"], c["pose"], c["voxel"] * c["ell"], c["depth_max"])
+    olocal = oracle.OracleMap(3, 1 << 17, [4])
+    ovol = oracle.OracleMap(3, 1 << 17, [8 * c["ell"] ** 3, 8 * c["ell"] ** 3])
+    _, _, ogi = oracle.double_map_activate(olocal, ovol, okeys)
+    oracle.tsdf_integrate(ovol, ogi, c["depth"], c["intr"], c["pose"], c["voxel"], c["trunc"], c["depth_max"],
+                          ell=c["ell"])
+    t_int = time.perf_counter() - t0
+    pix = np.arange(0, cam.width * cam.height, 97, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.tsdf_raycast(ovol, c["intr"], c["pose"], cam.width, cam.height, c["voxel"], c["depth_min"], c["step"],
+                        c["n_steps"], pixels=pix, ell=c["ell"], value_bytes=8)
+    t_rc = (time.perf_counter() - t0) * (cam.width * cam.height) / len(pix)
+    return {"ms_per_frame": 1000.0 * (t_int + t_rc), "cores": 1, "kind": "oracle",
+            "sample": "frame 0 of the voxel-block pipeline: keys, double map and integration in full; ray casting "
+                      "on every 97th pixel, scaled to the image"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def main(argv=None):
     args = parse_args(argv)
@@ -734,16 +758,18 @@ def main(argv=None):
         except Exception as e:  # noqa: BLE001
             blocks = {"error": str(e)[:300]}
 
-    tsdf = None
+    tsdf, tsdf_cpu_inputs = None, None
     if not args.no_tsdf and not args.lean:
         try:
-            tsdf = tsdf_figures(args, device, hbm_peak, rank == 0 and world == 1 and not args.no_cpu)
+            tsdf, tsdf_cpu_inputs = tsdf_figures(args, device, hbm_peak, rank == 0 and world == 1 and not args.no_cpu)
         except Exception as e:  # noqa: BLE001
-            tsdf = {"error": str(e)[:300]}
+            tsdf, tsdf_cpu_inputs = {"error": str(e)[:300]}, None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.lean:
         cpu = cpu_baseline(args, pts_np)
+        if tsdf_cpu_inputs is not None:
+            cpu["tsdf_frame"] = cpu_baseline_tsdf_frame(tsdf_cpu_inputs)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1010,25 +1036,11 @@ def tsdf_figures(args, device, hbm_peak, with_cpu):
     ms_global, ms_local = timed_rc(False), timed_rc(True)
     res["raycast_global_vs_local"] = {"ms_global_map": ms_global, "ms_local_map": ms_local,
                                       "speedup": ms_global / ms_local if ms_local else None}
-    if with_cpu:
-        import oracle
-        d = depths[0].cpu().numpy()
-        t0 = time.time()
-        okeys = oracle.depth_to_block_keys(d, intr, poses[0], voxel * ell, depth_max)
-        olocal = oracle.OracleMap(3, 1 << 17, [4])
-        ovol = oracle.OracleMap(3, 1 << 17, [8 * ell ** 3, 8 * ell ** 3])
-        _, _, ogi = oracle.double_map_activate(olocal, ovol, okeys)
-        oracle.tsdf_integrate(ovol, ogi, d, intr, poses[0], voxel, trunc, depth_max, ell=ell)
-        t_int = time.time() - t0
-        pix = np.arange(0, cam.width * cam.height, 97, dtype=np.int64)
-        t0 = time.time()
-        oracle.tsdf_raycast(ovol, intr, poses[0], cam.width, cam.height, voxel, depth_min, step, n_steps, pixels=pix,
-                            ell=ell, value_bytes=8)
-        t_rc = (time.time() - t0) * (cam.width * cam.height) / len(pix)
-        res["cpu_oracle"] = {"ms_per_frame": 1000.0 * (t_int + t_rc), "cores": 1,
-                             "sample": "frame 0: keys, double map and integration in full; ray casting on every "
-                                       "97th pixel, scaled to the image"}
-    return res
+    # inputs for the CPU oracle's timing of one frame (run by the cpu_baseline leg)
+    cpu_inputs = {"depth": depths[0].cpu().numpy(), "pose": poses[0], "intr": intr, "cam": cam, "voxel": voxel,
+                  "ell": ell, "trunc": trunc, "depth_max": depth_max, "depth_min": depth_min, "step": step,
+                  "n_steps": n_steps} if with_cpu else None
+    return res, cpu_inputs
 
 
 def per_op_figures(args, device, hbm_peak):
