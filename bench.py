@@ -1227,9 +1227,11 @@ def _pct(xs, q):
 def serving_figures(args, device, n_tenants=16, clients=8):
     """Poisson arrivals over 16 resident tenant maps (int32x3 keys, one f32
     value), request sizes log-uniform in 1e3..1e6 keys, ops 30/60/10
-    insert/find/erase.  Served form: the native continuous-batching server,
-    `clients` threads submitting at their scheduled arrival times (staged,
-    and, where the device reads pageable host memory, zero-copy).  Baseline:
+    insert/find/erase; request keys and values in pinned host memory.  Served
+    form: the native continuous-batching server, `clients` threads submitting
+    at their scheduled arrival times (staged with a copy at submit; staged
+    with DMA straight from the pinned request arrays; and, where the device
+    reads pageable host memory, zero-copy).  Baseline:
     the same requests as sequential plain calls (upload, op, download) in
     arrival order.  Latency = outputs on the host - scheduled arrival."""
     import threading
@@ -1237,8 +1239,10 @@ def serving_figures(args, device, n_tenants=16, clients=8):
     from paper_2110_00511_gb300 import ash
     rng = np.random.default_rng(5)
     pool_n = 8_000_000
-    key_pool = rng.integers(-(1 << 18), 1 << 18, size=(pool_n, 3)).astype(np.int32)
-    val_pool = rng.random(pool_n, dtype=np.float32)
+    # request data lives in pinned host memory, as a serving frontend would
+    # keep it (every form reads the same arrays)
+    key_pool = torch.from_numpy(rng.integers(-(1 << 18), 1 << 18, size=(pool_n, 3)).astype(np.int32)).pin_memory().numpy()
+    val_pool = torch.from_numpy(rng.random(pool_n, dtype=np.float32)).pin_memory().numpy()
     ops_of = np.array([ash.ASH_OP_INSERT, ash.ASH_OP_FIND, ash.ASH_OP_ERASE])
     rates = [float(x) for x in args.serving_rates.split(",") if x]
     R = args.serving_requests
@@ -1259,6 +1263,9 @@ def serving_figures(args, device, n_tenants=16, clients=8):
 
     srv = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
                      device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256)
+    srv_dma = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
+                         device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
+                         zero_copy=2)
     zc = ash.ash_get_device_info(device.index)["pageable_memory_access"] == 1
     srv_zc = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
                         device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
@@ -1321,6 +1328,7 @@ def serving_figures(args, device, n_tenants=16, clients=8):
     # warm both forms (pinned staging classes, device pools, first growth) untimed
     warm = make_trace(1000.0, 99)
     run_served(*warm)
+    run_served(*warm, srv=srv_dma)
     if srv_zc is not None:
         run_served(*warm, srv=srv_zc)
     run_sequential(*warm)
@@ -1335,6 +1343,14 @@ def serving_figures(args, device, n_tenants=16, clients=8):
         served["avg_requests_per_batch"] = (st1["batched_requests"] - st0["batched_requests"]) / max(1, nb)
         served["growth_rehashes"] = st1["rehashes"] - st0["rehashes"]
         entry = {"served": served}
+        d0 = srv_dma.stats()
+        dlat, dspan = run_served(*trace, srv=srv_dma)
+        d1 = srv_dma.stats()
+        ds = summarize(dlat, keys_total, dspan)
+        db = d1["batches"] - d0["batches"]
+        ds["avg_requests_per_batch"] = (d1["batched_requests"] - d0["batched_requests"]) / max(1, db)
+        ds["growth_rehashes"] = d1["rehashes"] - d0["rehashes"]
+        entry["served_pinned_dma"] = ds
         if srv_zc is not None:
             z0 = srv_zc.stats()
             zlat, zspan = run_served(*trace, srv=srv_zc)
@@ -1349,6 +1365,7 @@ def serving_figures(args, device, n_tenants=16, clients=8):
         entry["offered_keys_per_s"] = keys_total / float(trace[0][-1])
         out["rates"][str(int(rate))] = entry
     srv.close()
+    srv_dma.close()
     if srv_zc is not None:
         srv_zc.close()
     del maps

@@ -354,12 +354,19 @@ typedef struct ash_server_config {
   int64_t staging_bytes;      /* HBM budget for admitted requests' device buffers */
   float max_load;             /* grow before live/capacity would pass this (0.7) */
   int32_t max_batch_requests; /* requests per batch, 1..256 */
-  int32_t zero_copy;          /* 1: no staging.  The kernels read each request's keys and values from
+  int32_t zero_copy;          /* 0: keys and values are copied into pinned staging at submit (the
+                                 caller may reuse its arrays at once).
+                                 1: no staging.  The kernels read each request's keys and values from
                                  the caller's host arrays and write buf_indices / masks into the
                                  caller's arrays in place (devices with pageable memory access only,
                                  see ash_get_device_info); all four arrays must stay valid and
                                  unmodified from submit until wait returns.  Requests then take no
-                                 device staging and are admitted at once. */
+                                 device staging and are admitted at once.  Lowest latency below
+                                 saturation.
+                                 2: as 0, except that keys and values in page-locked (pinned) host
+                                 memory are uploaded by DMA straight from the caller's arrays, with
+                                 no CPU copy; those arrays must stay valid and unmodified until wait
+                                 returns.  Other requests behave as in mode 0. */
 } ash_server_config;
 typedef struct ash_server_stats {
   int64_t submitted;

@@ -128,6 +128,17 @@ class PinnedPool {
   std::map<int64_t, std::vector<void*>> spill_;     // cudaMallocHost blocks by size
 };
 
+// Page-locked (pinned or registered) host memory, which copy engines read
+// directly.
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 struct Request {
   uint64_t id = 0;
   int tenant = 0;
@@ -138,6 +149,8 @@ struct Request {
   const int32_t* keys_user = nullptr;  // zero-copy: the caller's arrays, used in place
   const void* vals_user = nullptr;
   bool zero_copy = false;
+  bool direct_in = false;    // inputs uploaded by DMA from the caller's pinned arrays
+  int64_t host_out_off = 0;  // offset of the outputs in the host staging block
   // staging: [keys | values | idx | mask], each 256-byte aligned
   int64_t off_keys = 0, off_vals = 0, off_idx = 0, off_mask = 0, bytes = 0;
   void* host = nullptr;
@@ -305,8 +318,16 @@ void worker_loop(ash_server* s) {
           st = ASH_ERR_OOM;
           break;
         }
-        const int64_t in_bytes = r->off_idx;  // keys and values precede the outputs
-        cudaMemcpyAsync(r->dev, r->host, in_bytes, cudaMemcpyHostToDevice, s->s_h2d);
+        if (r->direct_in) {
+          const int64_t kb = r->n * s->cfg.key_dim * 4;
+          cudaMemcpyAsync(r->dev + r->off_keys, r->keys_user, kb, cudaMemcpyHostToDevice, s->s_h2d);
+          if (r->vals_user)
+            cudaMemcpyAsync(r->dev + r->off_vals, r->vals_user, r->n * s->value_bytes, cudaMemcpyHostToDevice,
+                            s->s_h2d);
+        } else {
+          const int64_t in_bytes = r->off_idx;  // keys and values precede the outputs
+          cudaMemcpyAsync(r->dev, r->host, in_bytes, cudaMemcpyHostToDevice, s->s_h2d);
+        }
         ash_batch_op o{};
         o.map = s->maps[r->tenant];
         o.op = r->op;
@@ -337,7 +358,7 @@ void worker_loop(ash_server* s) {
         for (Request* r : pick) {
           if (r->zero_copy) continue;  // the kernels wrote the caller's arrays
           const int64_t out_bytes = r->bytes - r->off_idx;
-          cudaMemcpyAsync(static_cast<char*>(r->host) + r->off_idx, r->dev + r->off_idx, out_bytes,
+          cudaMemcpyAsync(static_cast<char*>(r->host) + r->host_out_off, r->dev + r->off_idx, out_bytes,
                           cudaMemcpyDeviceToHost, s->s_d2h);
         }
       }
@@ -409,8 +430,8 @@ ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host
   if (cfg->initial_capacity < 1 || cfg->staging_bytes < (1 << 20)) return fail(ASH_ERR_INVALID, "bad capacity or budget");
   if (!(cfg->max_load > 0.05f && cfg->max_load <= 1.0f)) return fail(ASH_ERR_INVALID, "max_load must be in (0.05, 1]");
   if (cfg->max_batch_requests < 1 || cfg->max_batch_requests > 256) return fail(ASH_ERR_INVALID, "max_batch_requests in 1..256");
-  if (cfg->zero_copy != 0 && cfg->zero_copy != 1) return fail(ASH_ERR_INVALID, "zero_copy must be 0 or 1");
-  if (cfg->zero_copy) {
+  if (cfg->zero_copy < 0 || cfg->zero_copy > 2) return fail(ASH_ERR_INVALID, "zero_copy must be 0, 1 or 2");
+  if (cfg->zero_copy == 1) {
     ash_device_info info{};
     ash_status ds = ash_get_device_info(cfg->device, &info);
     if (ds != ASH_OK) return ds;
@@ -420,7 +441,7 @@ ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host
   std::unique_ptr<ash_server> s(new ash_server());
   s->cfg = *cfg;
   s->value_bytes = cfg->value_row_bytes;
-  if (!cfg->zero_copy) s->pinned.reserve(cfg->staging_bytes);  // host staging as large as the device budget
+  if (cfg->zero_copy != 1) s->pinned.reserve(cfg->staging_bytes);  // host staging as large as the device budget
   DeviceGuard g(cfg->device);
   if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
@@ -473,7 +494,7 @@ ash_status ash_server_submit(ash_server* s, int32_t tenant, int32_t op, const in
   r->mask_user = masks_host;
   const int64_t kb = n * s->cfg.key_dim * 4;
   const int64_t vb = (op == ASH_OP_INSERT) ? n * s->value_bytes : 0;
-  if (s->cfg.zero_copy) {
+  if (s->cfg.zero_copy == 1) {
     r->zero_copy = true;
     r->keys_user = keys_host;
     r->vals_user = vb ? values_host : nullptr;
@@ -494,10 +515,21 @@ ash_status ash_server_submit(ash_server* s, int32_t tenant, int32_t op, const in
   r->off_idx = r->off_vals + align256(vb);
   r->off_mask = r->off_idx + align256(n * 4);
   r->bytes = r->off_mask + align256(n);
-  r->host = s->pinned.take(r->bytes, &r->host_cls);
-  if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
-  std::memcpy(static_cast<char*>(r->host) + r->off_keys, keys_host, kb);
-  if (vb) std::memcpy(static_cast<char*>(r->host) + r->off_vals, values_host, vb);
+  // mode 2: pinned input arrays are uploaded by DMA straight from the caller
+  r->direct_in = s->cfg.zero_copy == 2 && is_pinned(keys_host) && (!vb || is_pinned(values_host));
+  if (r->direct_in) {
+    r->keys_user = keys_host;
+    r->vals_user = vb ? values_host : nullptr;
+    r->host_out_off = 0;  // the host block holds only the outputs
+    r->host = s->pinned.take(r->bytes - r->off_idx, &r->host_cls);
+    if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
+  } else {
+    r->host_out_off = r->off_idx;
+    r->host = s->pinned.take(r->bytes, &r->host_cls);
+    if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
+    std::memcpy(static_cast<char*>(r->host) + r->off_keys, keys_host, kb);
+    if (vb) std::memcpy(static_cast<char*>(r->host) + r->off_vals, values_host, vb);
+  }
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -535,8 +567,9 @@ ash_status ash_server_wait(ash_server* s, uint64_t request_id, int64_t timeout_m
     return fail(werr, "the serving worker failed a batch: " + wmsg);
   }
   if (!r->zero_copy) {
-    if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, static_cast<char*>(r->host) + r->off_idx, r->n * 4);
-    std::memcpy(r->mask_user, static_cast<char*>(r->host) + r->off_mask, r->n);
+    const char* out = static_cast<char*>(r->host) + r->host_out_off;
+    if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, out, r->n * 4);
+    std::memcpy(r->mask_user, out + (r->off_mask - r->off_idx), r->n);
     s->pinned.give(r->host, r->host_cls);
   }
   if (latency_ms_host)

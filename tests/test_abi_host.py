@@ -84,7 +84,7 @@ def test_server_config_validation():
     L = ash.lib()
     out = ctypes.c_void_p()
     for field, bad in (("n_tenants", 0), ("key_dim", 5), ("value_row_bytes", 12), ("max_load", 0.0),
-                       ("max_batch_requests", 0), ("zero_copy", 2)):
+                       ("max_batch_requests", 0), ("zero_copy", 3)):
         c = ash.ash_server_default_config()
         setattr(c, field, bad)
         _err(L.ash_server_create(ctypes.byref(c), ctypes.byref(out)))

@@ -65,14 +65,22 @@ def _check_same(reqs, served, alone, server_maps, alone_maps):
             assert (si[~sm] == -1).all()
 
 
-@pytest.mark.parametrize("zero_copy", [0, 1])
+def _pinned(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("zero_copy", [0, 1, 2])
 def test_served_results_equal_alone_and_oracle(zero_copy):
-    """Staged, and zero-copy (the kernels read the caller's arrays in place,
-    on devices with pageable host memory access)."""
-    if zero_copy and ash.ash_get_device_info(0)["pageable_memory_access"] != 1:
+    """Staged (0), zero-copy (1: the kernels read the caller's arrays in
+    place, on devices with pageable host memory access), and DMA from the
+    caller's pinned arrays (2; every other request pinned, the rest copied)."""
+    if zero_copy == 1 and ash.ash_get_device_info(0)["pageable_memory_access"] != 1:
         pytest.skip("no pageable memory access on this device")
     n_t = 4
     reqs = _trace(1, 80, n_t)
+    if zero_copy == 2:
+        reqs = [(t, op, _pinned(k), _pinned(v)) if j % 2 == 0 else (t, op, k, v)
+                for j, (t, op, k, v) in enumerate(reqs)]
     srv = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=2048, value_row_bytes=4,
                      staging_bytes=64 << 20, max_load=0.7, max_batch_requests=256, zero_copy=zero_copy)
     ids = [srv.submit(t, OPS[op], keys, vals) for t, op, keys, vals in reqs]  # all in flight
@@ -129,7 +137,7 @@ def test_zero_copy_refused_without_pageable_access():
         with pytest.raises(ash.AshError):
             ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=1)
     with pytest.raises(ash.AshError):
-        ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=2)
+        ash.Server(n_tenants=1, key_dim=3, initial_capacity=1024, zero_copy=3)
 
 
 def test_server_rejects_bad_requests():
