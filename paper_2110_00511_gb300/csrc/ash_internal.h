@@ -60,6 +60,11 @@ struct ash_map {
   cudaStream_t insert_stream = nullptr;
   bool insert_streams_mixed = false;
   bool any_insert = false;
+  // Every key of the table sits in its preferred slot or that slot is
+  // occupied (the preferred-slot invariant), so an insert may CAS the
+  // preferred slot blindly.  Set by create, clear and every table rebuild;
+  // cleared by batched inserts, which place keys in slot order.
+  bool pref_placed = true;
   ash_tuning tuning{};
   ash::DimKernels K{};
   ash::host::Allocator alloc;
@@ -87,6 +92,7 @@ ash_status fail(ash_status s, const std::string& msg);
 ash_status cuda_fail(cudaError_t e, const char* where);
 ash_status check_launch(const char* where);
 int sm_count(int device);
+int64_t l2_bytes(int device);
 int vec_width(int64_t row_bytes, const void* a, const void* b);
 void* dev_alloc(ash_map* m, size_t bytes, cudaStream_t st);
 void dev_free(ash_map* m, void* p, cudaStream_t st);

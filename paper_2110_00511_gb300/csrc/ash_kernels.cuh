@@ -277,13 +277,13 @@ __device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_
   return kb_equal<D>(kb, lo, k) ? 2 : 0;
 }
 
-// The full claim protocol for one key, from its home bucket (the slow path of
-// the claim kernel; safe to run after a fast-path attempt that changed
-// nothing).  1) any slot of the bucket holding an equal key ends the search;
-// 2) otherwise the EMPTY slots are claimed in order, and a lost CAS re-checks
+// The full claim protocol for one key, from its home bucket: 1) any slot of
+// the bucket holding an equal key ends the search; 2) otherwise the EMPTY
+// slots are claimed in order (PrefFirst: the preferred one first in the home
+// bucket, which keeps the preferred-slot invariant), and a lost CAS re-checks
 // the winner's word for an equal key; 3) a bucket without EMPTY slots sends
 // the key to the next bucket.
-template <int D, int S, class In>
+template <int D, int S, class In, bool PrefFirst = true>
 __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
@@ -305,20 +305,23 @@ __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys,
         return static_cast<int32_t>(b * S + s);
       }
     }
+    // EMPTY slots of the snapshot as a bit mask (one CAS site for all)
+    uint32_t emask = 0;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      if (w[s] == kEmpty) {
-        const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(bp + s),
-                                       static_cast<unsigned long long>(kEmpty),
-                                       static_cast<unsigned long long>(mine));
-        if (old == kEmpty) return static_cast<int32_t>(b * S + s);
-        const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
-        if (m == 2) return kClaimExists;
-        if (m == 1) {
-          if ((lo32(old) & ~kClaimBit) > static_cast<uint32_t>(pos))
-            atomicMin(reinterpret_cast<unsigned long long*>(bp + s), static_cast<unsigned long long>(mine));
-          return static_cast<int32_t>(b * S + s);
-        }
+    for (int s = 0; s < S; ++s) emask |= (w[s] == kEmpty ? 1u : 0u) << s;
+    const uint32_t pbit = PrefFirst && probe == 0 ? 1u << pref_slot<S>(fp) : 0u;
+    while (emask) {
+      const int s = (emask & pbit) ? static_cast<int>(pref_slot<S>(fp)) : __ffs(emask) - 1;
+      emask &= ~(1u << s);
+      const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(bp + s),
+                                     static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+      if (old == kEmpty) return static_cast<int32_t>(b * S + s);
+      const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
+      if (m == 2) return kClaimExists;
+      if (m == 1) {
+        if ((lo32(old) & ~kClaimBit) > static_cast<uint32_t>(pos))
+          atomicMin(reinterpret_cast<unsigned long long*>(bp + s), static_cast<unsigned long long>(mine));
+        return static_cast<int32_t>(b * S + s);
       }
     }
     b = next_bucket(b, t.n_buckets);
@@ -327,30 +330,189 @@ __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys,
   return kClaimFailed;
 }
 
-// Out-of-line copy of the full protocol: the rare slow path of claim_kernel
-// (kept out of line so it does not raise the fast path's register count).
+// Out-of-line copy of the full protocol: the rare slow path of the claim
+// kernels (kept out of line so it does not raise their register count).
 template <int D, int S, class In>
 __device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int64_t pos) {
   return claim_key<D, S, In>(t, keys, pos);
 }
 
-// KPT keys per thread.  Fast path per key, on its home bucket only: if the
-// bucket holds exactly one slot with the key's fingerprint, compare once
-// (claimant's input row or kB row); on no match, CAS the first EMPTY slot.
-// The loads, compares and CASes of the KPT keys are issued back to back.
-// Anything else (several fingerprint matches, a lost CAS, a full bucket)
-// runs claim_one, which is safe because the fast path changed nothing then.
-template <int D, int S, int KPT, class In = const int32_t*>
-__global__ void __launch_bounds__(256) claim_kernel(TableView t, const In keys, int64_t n,
-                                                    int32_t* __restrict__ slot_out) {
+// Claim from the loaded home bucket, DK keys per lane (pos[q] valid where
+// v[q]).  Per key: if the bucket holds exactly one slot with the key's
+// fingerprint, compare once (claimant's input row or kB row); on no match,
+// CAS the preferred slot if it is EMPTY, else the first EMPTY slot.
+// The loads, compares and CASes of the DK keys are issued back to back.
+// Anything else (several fingerprint matches, a lost CAS, a full bucket) runs
+// claim_one, which is safe because this path changed nothing then.
+template <int D, int S, int DK, class In>
+__device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& keys, const int64_t (&pos)[DK],
+                                                  const bool (&v)[DK], int32_t* __restrict__ slot_out) {
   constexpr int KS = KeyStride<D>::value;
+  int32_t k[DK][D];
+  uint32_t fp[DK], b[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    if (v[q]) {
+      load_input_key<D>(keys, pos[q], k[q]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) k[q][j] = 0;
+    }
+    const uint64_t h = hash_key<D>(k[q]);
+    fp[q] = fingerprint(h);
+    b[q] = home_bucket(h, t.n_buckets);
+  }
+  uint64_t w[DK][S];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    if (v[q]) {
+      load_bucket<S, false>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) w[q][s] = kTombstone;
+    }
+  }
+  int cs[DK], nc[DK], es[DK];
+  uint32_t clo[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    cs[q] = -1;
+    nc[q] = 0;
+    es[q] = -1;
+    clo[q] = kNoIndex;
+    const uint32_t pref = pref_slot<S>(fp[q]);
+    int pe = -1;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const bool m = lo32(w[q][s]) != kNoIndex && hi32(w[q][s]) == fp[q];
+      if (m && nc[q] == 0) {
+        cs[q] = s;
+        clo[q] = lo32(w[q][s]);
+      }
+      nc[q] += m ? 1 : 0;
+      if (es[q] < 0 && w[q][s] == kEmpty) es[q] = s;
+      if (static_cast<uint32_t>(s) == pref && w[q][s] == kEmpty) pe = s;
+    }
+    if (pe >= 0) es[q] = pe;  // preferred slot first (preferred-slot invariant)
+  }
+  int32_t row[DK][KS];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    if (nc[q] > 0) {
+      if (clo[q] & kClaimBit) {
+        int32_t o[D];
+        load_input_key<D>(keys, clo[q] & ~kClaimBit, o);
+#pragma unroll
+        for (int j = 0; j < KS; ++j) row[q][j] = j < D ? o[j] : 0;
+      } else {
+        load_kb<D>(t.kb, clo[q], row[q]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < KS; ++j) row[q][j] = 0;
+    }
+  }
+  int32_t res[DK];
+  bool cas[DK], slow[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    res[q] = kClaimFailed;
+    cas[q] = false;
+    slow[q] = false;
+    if (v[q]) {
+      bool eq = nc[q] > 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
+      if (eq) {
+        if (clo[q] & kClaimBit) {
+          if ((clo[q] & ~kClaimBit) > static_cast<uint32_t>(pos[q])) {
+            const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos[q]));
+            atomicMin(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + cs[q]),
+                      static_cast<unsigned long long>(mine));
+          }
+          res[q] = static_cast<int32_t>(b[q] * S + cs[q]);
+        } else {
+          res[q] = kClaimExists;
+        }
+      } else if (nc[q] > 1 || es[q] < 0) {
+        slow[q] = true;
+      } else {
+        cas[q] = true;
+      }
+    }
+  }
+  uint64_t old[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    old[q] = 0;
+    if (cas[q]) {
+      const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos[q]));
+      old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + es[q]),
+                         static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    if (cas[q]) {
+      if (old[q] == kEmpty) res[q] = static_cast<int32_t>(b[q] * S + es[q]);
+      else slow[q] = true;
+    }
+    if (slow[q]) res[q] = claim_one<D, S, In>(t, keys, pos[q]);  // rare
+    if (v[q]) slot_out[pos[q]] = res[q];
+  }
+}
+
+// Claim kernel, bucket load first: KPT keys per thread, each claimed from its
+// loaded home bucket (two dependent accesses per key: bucket load, CAS).  The
+// better choice when the table does not stay in L2: the loads bring the
+// buckets in with deep miss queues and the CASes then hit L2.
+template <int D, int S, int KPT, class In = const int32_t*>
+__global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In keys, int64_t n,
+                                                           int32_t* __restrict__ slot_out) {
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT + threadIdx.x; base < n; base += step) {
-    int32_t k[KPT][D];
-    uint32_t fp[KPT], b[KPT];
+    int64_t p[KPT];
+    bool v[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      p[q] = base + static_cast<int64_t>(q) * blockDim.x;
+      v[q] = p[q] < n;
+    }
+    claim_from_bucket<D, S, KPT, In>(t, keys, p, v, slot_out);
+  }
+}
+
+// Claim kernel, preferred slot first.  Each warp takes 32 * KPT consecutive keys per iteration
+// (KPT per lane).  Fast path per key: CAS the preferred slot of the home
+// bucket, with no bucket load before it.  EMPTY there: claimed.  An occupant
+// with the key's fingerprint: compare once (claimant's input row or kB row);
+// an equal key joins the claim (lowest position wins) or reports the
+// committed key.  Any other key (the preferred slot holds another key, a
+// tombstone, or a fingerprint collision) is queued in the warp's shared-memory
+// list; whenever the list holds 64 keys the warp claims them from their
+// buckets together, two per lane (claim_from_bucket), so the slower path runs
+// on dense warps instead of stalling every warp for a few lanes.
+// A CAS that misses L2 waits on DRAM inside the atomic unit, so this path
+// pays off while the table stays in L2.
+template <int D, int S, int KPT, class In = const int32_t*>
+__global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In keys, int64_t n,
+                                                         int32_t* __restrict__ slot_out) {
+  constexpr int KS = KeyStride<D>::value;
+  constexpr int kDrain = 64;                 // queued keys claimed per dense round (2 per lane)
+  constexpr int kCap = kDrain + 32 * KPT;    // a round starts before a tile could overflow
+  __shared__ int32_t s_queue[8][kCap];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t* queue = s_queue[threadIdx.x >> 5];
+  int qn = 0;  // warp-uniform
+  const int64_t n_warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int64_t warp_id = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t wbase = warp_id * 32 * KPT; wbase < n; wbase += n_warps * 32 * KPT) {
+    int32_t k[KPT][D];
+    uint32_t fp[KPT], ps[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = wbase + q * 32 + lane;
       if (pos < n) {
         load_input_key<D>(keys, pos, k[q]);
       } else {
@@ -359,98 +521,90 @@ __global__ void __launch_bounds__(256) claim_kernel(TableView t, const In keys, 
       }
       const uint64_t h = hash_key<D>(k[q]);
       fp[q] = fingerprint(h);
-      b[q] = home_bucket(h, t.n_buckets);
+      ps[q] = home_bucket(h, t.n_buckets) * S + pref_slot<S>(fp[q]);
     }
-    uint64_t w[KPT][S];
-#pragma unroll
-    for (int q = 0; q < KPT; ++q) load_bucket<S, false>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
-    int cs[KPT], nc[KPT], es[KPT];
-    uint32_t clo[KPT];
+    uint64_t old[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-      cs[q] = -1;
-      nc[q] = 0;
-      es[q] = -1;
-      clo[q] = kNoIndex;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const bool m = lo32(w[q][s]) != kNoIndex && hi32(w[q][s]) == fp[q];
-        if (m && nc[q] == 0) {
-          cs[q] = s;
-          clo[q] = lo32(w[q][s]);
-        }
-        nc[q] += m ? 1 : 0;
-        if (es[q] < 0 && w[q][s] == kEmpty) es[q] = s;
+      const int64_t pos = wbase + q * 32 + lane;
+      old[q] = kTombstone;
+      if (pos < n) {
+        const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
+        old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + ps[q]),
+                           static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
       }
     }
+    bool fm[KPT];
     int32_t row[KPT][KS];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-      if (nc[q] > 0) {
-        if (clo[q] & kClaimBit) {
+      const uint32_t lo = lo32(old[q]);
+      fm[q] = lo != kNoIndex && hi32(old[q]) == fp[q];
+      if (fm[q]) {
+        if (lo & kClaimBit) {
           int32_t o[D];
-          load_input_key<D>(keys, clo[q] & ~kClaimBit, o);
+          load_input_key<D>(keys, lo & ~kClaimBit, o);
 #pragma unroll
           for (int j = 0; j < KS; ++j) row[q][j] = j < D ? o[j] : 0;
         } else {
-          load_kb<D>(t.kb, clo[q], row[q]);
+          load_kb<D>(t.kb, lo, row[q]);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < KS; ++j) row[q][j] = 0;
       }
     }
-    int32_t res[KPT];
-    bool cas[KPT], slow[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-      res[q] = kClaimFailed;
-      cas[q] = false;
-      slow[q] = false;
+      const int64_t pos = wbase + q * 32 + lane;
+      bool pending = false;
       if (pos < n) {
-        bool eq = nc[q] > 0;
+        const uint32_t lo = lo32(old[q]);
+        bool eq = fm[q];
 #pragma unroll
         for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
-        if (eq) {
-          if (clo[q] & kClaimBit) {
-            if ((clo[q] & ~kClaimBit) > static_cast<uint32_t>(pos)) {
-              const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
-              atomicMin(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + cs[q]),
-                        static_cast<unsigned long long>(mine));
-            }
-            res[q] = static_cast<int32_t>(b[q] * S + cs[q]);
-          } else {
-            res[q] = kClaimExists;
+        if (old[q] == kEmpty) {
+          slot_out[pos] = static_cast<int32_t>(ps[q]);
+        } else if (!eq) {
+          pending = true;
+        } else if (lo & kClaimBit) {
+          if ((lo & ~kClaimBit) > static_cast<uint32_t>(pos)) {
+            const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
+            atomicMin(reinterpret_cast<unsigned long long*>(t.slots + ps[q]), static_cast<unsigned long long>(mine));
           }
-        } else if (nc[q] > 1 || es[q] < 0) {
-          slow[q] = true;
+          slot_out[pos] = static_cast<int32_t>(ps[q]);
         } else {
-          cas[q] = true;
+          slot_out[pos] = kClaimExists;
         }
       }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, pending);
+      if (pending) queue[qn + __popc(bal & lt)] = static_cast<int32_t>(pos);
+      qn += __popc(bal);
     }
-    uint64_t old[KPT];
+    __syncwarp();
+    while (qn >= kDrain) {
+      int64_t p[2];
+      bool v[2];
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      old[q] = 0;
-      if (cas[q]) {
-        const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-        const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
-        old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + es[q]),
-                           static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+      for (int r = 0; r < 2; ++r) {
+        v[r] = true;
+        p[r] = queue[qn - kDrain + r * 32 + lane];
       }
+      __syncwarp();
+      qn -= kDrain;
+      claim_from_bucket<D, S, 2, In>(t, keys, p, v, slot_out);
     }
+  }
+  __syncwarp();
+  if (qn > 0) {
+    int64_t p[2];
+    bool v[2];
 #pragma unroll
-    for (int q = 0; q < KPT; ++q) {
-      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-      if (cas[q]) {
-        if (old[q] == kEmpty) res[q] = static_cast<int32_t>(b[q] * S + es[q]);
-        else slow[q] = true;
-      }
-      if (slow[q]) res[q] = claim_one<D, S, In>(t, keys, pos);  // rare
-      if (pos < n) slot_out[pos] = res[q];
+    for (int r = 0; r < 2; ++r) {
+      v[r] = r * 32 + lane < qn;
+      p[r] = v[r] ? queue[r * 32 + lane] : 0;
     }
+    claim_from_bucket<D, S, 2, In>(t, keys, p, v, slot_out);
   }
 }
 
@@ -623,10 +777,25 @@ __device__ __forceinline__ void erase_resolve_tile(const TableView& t, int64_t n
     w = load_slot_relaxed(t.slots + s);
     win = hi32(w) == static_cast<uint32_t>(pos);
     if (win) {
-      uint64_t bw[S];
-      load_bucket<S, false>(t.slots + static_cast<size_t>(s / S) * S, bw);
+      // EMPTY only when the bucket already has an EMPTY slot (no probe chain
+      // passes through it) and no other live key of the bucket prefers the
+      // freed slot (the preferred-slot invariant); a TOMBSTONE otherwise.
+      // (the freed slot itself holds a marked word, which never counts).  The
+      // bucket is read 32 bytes at a time to keep few words live.
+      const uint64_t* bp = t.slots + static_cast<size_t>(s / S) * S;
+      const uint32_t own = static_cast<uint32_t>(s) & (S - 1);
+      bool preferred = false;
+#pragma unroll 1
+      for (int c = 0; c < S / 4; ++c) {
+        uint64_t cw[4];
+        load32<false>(bp + 4 * c, cw[0], cw[1], cw[2], cw[3]);
 #pragma unroll
-      for (int q = 0; q < S; ++q) to_empty |= (bw[q] == kEmpty);
+        for (int j = 0; j < 4; ++j) {
+          to_empty |= (cw[j] == kEmpty);
+          preferred |= is_committed(cw[j]) && pref_slot<S>(hi32(cw[j])) == own;
+        }
+      }
+      to_empty &= !preferred;
     }
   }
   int rank, total;
@@ -688,7 +857,10 @@ __global__ void __launch_bounds__(256) rebuild_kernel(TableView t, const int32_t
     const uint64_t h = hash_key<D>(k);
     const uint64_t word = (static_cast<uint64_t>(fingerprint(h)) << 32) | i;
     uint32_t b = home_bucket(h, t.n_buckets);
-    bool placed = false;
+    // the preferred slot first (preferred-slot invariant), then the full probe
+    const uint32_t ps = b * S + pref_slot<S>(fingerprint(h));
+    bool placed = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + ps), static_cast<unsigned long long>(kEmpty),
+                            static_cast<unsigned long long>(word)) == kEmpty;
     for (uint32_t probe = 0; probe < t.max_probes && !placed; ++probe) {
       uint64_t* bp = t.slots + static_cast<size_t>(b) * S;
       uint64_t w[S];
@@ -725,7 +897,7 @@ inline int grid_for(int64_t n, const Launch& L) {
 // per bucket (4, 8, 16); kpt: keys per thread (1, 2, 4).
 struct DimKernels {
   void (*find)(int S, int kpt, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
-  void (*claim)(int S, int kpt, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
+  void (*claim)(int S, int kpt, int pref, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
   void (*commit)(int kpt, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const ValueRow*,
                  const Launch&);
   void (*erase_mark)(int S, const TableView&, const int32_t*, int64_t, int32_t*, const Launch&);
@@ -737,7 +909,7 @@ struct DimKernels {
   void (*find_group)(int S, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
   // the same operations on float32 points quantised in the kernels
   void (*find_pts)(int S, int kpt, const TableView&, const PointRows&, int64_t, int32_t*, uint8_t*, const Launch&);
-  void (*claim_pts)(int S, int kpt, const TableView&, const PointRows&, int64_t, int32_t*, const Launch&);
+  void (*claim_pts)(int S, int kpt, int pref, const TableView&, const PointRows&, int64_t, int32_t*, const Launch&);
   void (*commit_pts)(int kpt, const TableView&, const PointRows&, int64_t, int32_t*, uint8_t*, const ValueRow*,
                      const Launch&);
 };
@@ -771,31 +943,36 @@ struct DimLaunchers {
                        uint8_t* mask, const Launch& L) {
     find_in(S, kpt, t, p, n, idx, mask, L);
   }
+  // pref: 1 = preferred slot first (claim_pref_kernel), 0 = bucket load first
   template <int S, int KPT, class In>
-  static void claim_sk(const TableView& t, const In& keys, int64_t n, int32_t* slot_out, const Launch& L) {
+  static void claim_sk(int pref, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,
+                       const Launch& L) {
     TraceScope ts(kKClaim, L.stream);
-    claim_kernel<D, S, KPT, In><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    const int g = grid_for((n + KPT - 1) / KPT, L);
+    if (pref) claim_pref_kernel<D, S, KPT, In><<<g, L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    else claim_bucket_kernel<D, S, KPT, In><<<g, L.block, 0, L.stream>>>(t, keys, n, slot_out);
   }
   template <int S, class In>
-  static void claim_s(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* slot_out, const Launch& L) {
-    if (kpt >= 4) claim_sk<S, 4>(t, keys, n, slot_out, L);
-    else if (kpt == 2) claim_sk<S, 2>(t, keys, n, slot_out, L);
-    else claim_sk<S, 1>(t, keys, n, slot_out, L);
+  static void claim_s(int kpt, int pref, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,
+                      const Launch& L) {
+    if (kpt >= 4) claim_sk<S, 4>(pref, t, keys, n, slot_out, L);
+    else if (kpt == 2) claim_sk<S, 2>(pref, t, keys, n, slot_out, L);
+    else claim_sk<S, 1>(pref, t, keys, n, slot_out, L);
   }
   template <class In>
-  static void claim_in(int S, int kpt, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,
+  static void claim_in(int S, int kpt, int pref, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,
                        const Launch& L) {
-    if (S == 4) claim_s<4>(kpt, t, keys, n, slot_out, L);
-    else if (S == 8) claim_s<8>(kpt, t, keys, n, slot_out, L);
-    else claim_s<16>(kpt, t, keys, n, slot_out, L);
+    if (S == 4) claim_s<4>(kpt, pref, t, keys, n, slot_out, L);
+    else if (S == 8) claim_s<8>(kpt, pref, t, keys, n, slot_out, L);
+    else claim_s<16>(kpt, pref, t, keys, n, slot_out, L);
   }
-  static void claim(int S, int kpt, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out,
+  static void claim(int S, int kpt, int pref, const TableView& t, const int32_t* keys, int64_t n, int32_t* slot_out,
                     const Launch& L) {
-    claim_in(S, kpt, t, keys, n, slot_out, L);
+    claim_in(S, kpt, pref, t, keys, n, slot_out, L);
   }
-  static void claim_pts(int S, int kpt, const TableView& t, const PointRows& p, int64_t n, int32_t* slot_out,
-                        const Launch& L) {
-    claim_in(S, kpt, t, p, n, slot_out, L);
+  static void claim_pts(int S, int kpt, int pref, const TableView& t, const PointRows& p, int64_t n,
+                        int32_t* slot_out, const Launch& L) {
+    claim_in(S, kpt, pref, t, p, n, slot_out, L);
   }
   template <int KPT, bool VAL, class In>
   static void commit_kv(const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,

@@ -85,6 +85,17 @@ int64_t dtype_bytes(int32_t dt) {
   }
 }
 
+int64_t l2_bytes(int device) {
+  static int64_t cache[64] = {};
+  if (device < 0 || device >= 64) return 0;
+  if (cache[device] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device);
+    cache[device] = v > 0 ? v : 1;
+  }
+  return cache[device];
+}
+
 int sm_count(int device) {
   static int cache[64] = {};
   if (device < 0 || device >= 64) return 1;
@@ -151,6 +162,18 @@ ash::DimKernels kernels_for(int d) {
   }
 }
 
+// Claim protocol of an insert: the preferred-slot CAS first while the table
+// takes at most two thirds of L2 (a CAS that misses L2 waits on DRAM in the
+// atomic unit), else the bucket load first.  On GB300 (L2 135.5 MB) the
+// preferred-slot path is 6-25 % faster up to 80 MB tables, even at 96 MB and
+// 19 % slower at 128 MB.  It needs the preferred-slot invariant, which a
+// batched insert gives up until the next clear or rebuild.
+int claim_prefers_slot(const ash_map* m) {
+  if (m->tuning.claim_mode == 1 || !m->pref_placed) return 0;
+  if (m->tuning.claim_mode == 2) return 1;
+  return m->n_slots * 8 * 3 <= l2_bytes(m->device) * 2 ? 1 : 0;
+}
+
 ash::Launch launch_of(const ash_map* m, cudaStream_t st) {
   ash::Launch L;
   L.stream = st;
@@ -192,6 +215,7 @@ ash_status validate_tuning(const ash_tuning& t) {
   if (t.find_keys_per_thread != 0 && t.find_keys_per_thread != 1 && t.find_keys_per_thread != 2 &&
       t.find_keys_per_thread != 4)
     return fail(ASH_ERR_INVALID, "find_keys_per_thread must be 0, 1, 2 or 4");
+  if (t.claim_mode < 0 || t.claim_mode > 2) return fail(ASH_ERR_INVALID, "claim_mode must be 0, 1 or 2");
   return ASH_OK;
 }
 
@@ -306,6 +330,7 @@ ash_status alloc_storage(ash_map* m, int64_t capacity, cudaStream_t st) {
   m->n_slots = n_slots;
   m->S = m->tuning.slots_per_bucket;
   m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
+  m->pref_placed = true;
   ASH_CUDA(cudaMemsetAsync(m->slots, 0xFF, n_slots * 8, st));
   for (int j = 0; j < m->n_values; ++j) ASH_CUDA(cudaMemsetAsync(m->vb[j], 0, capacity * m->row_bytes[j], st));
   ash::launch_iota(m->heap, 0, capacity, L);
@@ -422,10 +447,11 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
       ash::launch_gather_rows(vc, list, size, L);
     }
   }
-  // 2) re-insert the live keys into the new table
+  // 2) re-insert the live keys into the new table (preferred slots first)
   m->S = m->tuning.slots_per_bucket;
   m->slots = slots;
   m->n_slots = n_slots;
+  m->pref_placed = true;
   m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
   m->capacity = new_capacity;
   m->kb = kb;
@@ -512,6 +538,7 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
   m->S = m->tuning.slots_per_bucket;
   m->slots = slots;
   m->n_slots = n_slots;
+  m->pref_placed = true;  // the rebuild below places keys preferred-first
   m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
   m->capacity = new_capacity;
   m->kb = kb;
@@ -578,8 +605,9 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   const ash::Launch L = launch_of(m, st);
   const ash::TableView tv = view_of(m);
   const int kpt = m->tuning.keys_per_thread;
-  if (pts) m->K.claim_pts(m->S, kpt, tv, *pts, n, idx, L);
-  else m->K.claim(m->S, kpt, tv, keys, n, idx, L);
+  const int pref = claim_prefers_slot(m);
+  if (pts) m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
+  else m->K.claim(m->S, kpt, pref, tv, keys, n, idx, L);
   // one value buffer with small rows: copied by the committing thread;
   // anything else: warp-per-row scatter after the commit
   bool inline_value = false;
@@ -635,6 +663,7 @@ void ash_default_tuning(ash_tuning* out) {
   out->keys_per_thread = 2;
   out->warp_probe = 0;
   out->find_keys_per_thread = 1;
+  out->claim_mode = 0;
 }
 
 ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {
@@ -925,6 +954,7 @@ ash_status ash_clear(ash_map* m, ash_stream stream) {
   ash::launch_set_top_used(m->ctrl, 0, 0, L);
   m->size_ub = 0;
   m->used_ub = 0;
+  m->pref_placed = true;
   invalidate_snapshot(m);
   return check_launch("clear");
 }

@@ -134,3 +134,37 @@ def test_autotune_returns_valid_cached_tuning():
     om = oracle.OracleMap(3, 1 << 16)
     oi, omask = om.activate(keys)
     assert_op_parity(hm, keys, gi, gm, oi, omask)
+
+
+@pytest.mark.parametrize("S", [4, 8])
+def test_batched_then_plain_inserts_with_preferred_slot_claims(S):
+    """Batched inserts place keys in slot order, outside the preferred-slot
+    invariant; plain inserts that follow (asked for the preferred-slot CAS,
+    claim_mode 2) must fall back to the bucket-first claim until a rehash or
+    clear restores the invariant, or they would store second copies of keys
+    the batch placed.  Dense buckets, erase churn, checked against the oracle
+    after every call."""
+    rng = np.random.default_rng(60 + S)
+    t = _tuning(S)
+    t.slots_per_capacity = 1.1
+    t.claim_mode = 2
+    hm = ash.HashMap(3, 3000, [(1,)], [torch.float32], tuning=t)
+    om = oracle.OracleMap(3, 3000, [4])
+    batch = ash.Batch(0)
+    for r in range(12):
+        k = rng.integers(-9, 9, size=(1500, 3)).astype(np.int32)
+        v = rng.random(1500, dtype=np.float32)
+        if r % 3 == 0:
+            (gi, gm), = batch.run([(hm, ash.ASH_OP_INSERT, dev(k), dev(v))])
+            torch.cuda.synchronize()
+        else:
+            gi, gm = hm.insert(dev(k), [dev(v)])
+        oi, omask = om.insert(k, [v])
+        assert_op_parity(hm, k, gi, gm, oi, omask)
+        e = rng.integers(-9, 9, size=(700, 3)).astype(np.int32)
+        assert np.array_equal(hm.erase(dev(e)).cpu().numpy(), om.erase(e))
+        if r == 7:
+            hm.rehash()
+            om.rehash()
+        assert_same_map(hm, om)
+    assert_heap_permutation(hm)

@@ -44,6 +44,9 @@ def test_random_sequences(seed):
     hm = ash.HashMap(d, cap, shapes, dtypes, tuning=t)
     om = oracle.OracleMap(d, cap, rbs)
     span = int(rng.integers(2, 40))
+    # the claim protocol switches between calls (its own generator, so the
+    # operation sequence of each seed does not depend on it)
+    mode_rng = np.random.default_rng(9000 + seed)
     for step in range(40):
         op = rng.choice(["insert", "activate", "find", "erase", "rehash", "reserve", "clear"],
                         p=[0.3, 0.15, 0.25, 0.2, 0.04, 0.03, 0.03])
@@ -51,6 +54,10 @@ def test_random_sequences(seed):
         keys = rng.integers(-span, span, size=(n, d)).astype(np.int32)
         if op == "activate" and vrow:
             op = "insert"
+        if op in ("insert", "activate"):
+            tt = hm.tuning()
+            tt.claim_mode = int(mode_rng.integers(0, 3))
+            hm.set_tuning(tt)
         if op == "insert":
             if vrow:
                 vals = rng.random((n, vrow // 4), dtype=np.float32)

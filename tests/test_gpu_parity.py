@@ -91,16 +91,18 @@ def test_dims_and_bucket_sizes(d, S):
 
 
 # ------------------------------------------------------------ race stress
-def test_duplicate_race_stress():
+@pytest.mark.parametrize("claim_mode", [1, 2])
+def test_duplicate_race_stress(claim_mode):
     """1M keys drawn from 1000 distinct triples (the heavy-duplicate setting
     where Sec. 4.4.2 reports torn-copy races): exactly one winner per key, the
-    first occurrence, with its own value; repeated on fresh maps."""
+    first occurrence, with its own value; repeated on fresh maps, under both
+    claim protocols (bucket load first; preferred-slot CAS first)."""
     rng = np.random.default_rng(5)
     distinct = rng.integers(-2**30, 2**30, size=(1000, 3)).astype(np.int32)
     for rep in range(5):
         keys = distinct[rng.integers(0, 1000, size=1_000_000)]
         vals = np.arange(1_000_000, dtype=np.int32)
-        hm = ash.HashMap(3, 1_000_000, [(1,)], [torch.int32])
+        hm = ash.HashMap(3, 1_000_000, [(1,)], [torch.int32], tuning=tuning(claim_mode=claim_mode))
         gi, gm = hm.insert(dev(keys), [dev(vals)])
         _, first = np.unique(keys, axis=0, return_index=True)
         want = np.zeros(len(keys), bool)
@@ -441,6 +443,37 @@ def test_churn_with_tombstones():
         assert_op_parity(hm, k, gi, gm, oi, omask)
         e = rng.integers(-15, 15, size=(900, 3)).astype(np.int32)
         assert np.array_equal(hm.erase(dev(e)).cpu().numpy(), om.erase(e))
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+@pytest.mark.parametrize("S", [4, 8])
+def test_claim_protocols_mixed_on_dense_buckets(S):
+    """Both claim protocols on one map with dense buckets (1.1 slots per unit
+    of capacity) under insert/erase churn, the protocol switching between
+    calls: erase must leave a tombstone where another live key of the bucket
+    prefers the freed slot, or a later preferred-slot CAS would store a second
+    copy of that key.  Checked against the oracle after every call."""
+    rng = np.random.default_rng(40 + S)
+    t = tuning(slots_per_bucket=S, slots_per_capacity=1.1)
+    hm = ash.HashMap(3, 6000, [(1,)], [torch.int32], tuning=t)
+    om = oracle.OracleMap(3, 6000, [4])
+    for r in range(30):
+        tt = hm.tuning()
+        tt.claim_mode = int(rng.integers(0, 3))
+        hm.set_tuning(tt)
+        k = rng.integers(-11, 11, size=(2500, 3)).astype(np.int32)
+        v = rng.integers(0, 1 << 20, size=2500).astype(np.int32)
+        gi, gm = hm.insert(dev(k), [dev(v)])
+        oi, omask = om.insert(k, [v])
+        assert_op_parity(hm, k, gi, gm, oi, omask)
+        e = rng.integers(-11, 11, size=(1500, 3)).astype(np.int32)
+        assert np.array_equal(hm.erase(dev(e)).cpu().numpy(), om.erase(e))
+        f = rng.integers(-12, 12, size=(3000, 3)).astype(np.int32)
+        fi, fm = hm.find(dev(f))
+        ofi, ofm = om.find(f)
+        assert_op_parity(hm, f, fi, fm, ofi, ofm, check_distinct=False)
+        assert hm.size() == om.size()
     assert_same_map(hm, om)
     assert_heap_permutation(hm)
 
