@@ -198,9 +198,14 @@ def bytes_commit(n, n_slotted, n_win, value_bytes, d=3):
     return n * 9 + n_slotted * 32 + n_win * (4 + 4 * d + 4 * key_stride(d) + 32 + 2 * value_bytes)
 
 
-def bytes_list(capacity, n_live):
-    """Heap tail read (4 per free index), free bitmap cleared, marked and read
-    (c/8 bytes each), live indices written (4 each)."""
+def bytes_list(capacity, n_live, heap_identity=True):
+    """A map with no erase since create, clear or a compacting rehash has the
+    identity as its heap's free part, so its live indices are 0..t-1 and the
+    listing only writes them (4 each).  Otherwise: heap tail read (4 per free
+    index), free bitmap cleared, marked and read (c/8 bytes each), live
+    indices written (4 each)."""
+    if heap_identity:
+        return 4 * n_live
     return 4 * (capacity - n_live) + 3 * ((capacity + 7) // 8) + 4 * n_live
 
 

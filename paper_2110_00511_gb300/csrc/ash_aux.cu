@@ -94,8 +94,36 @@ int64_t list_scratch_words(int64_t capacity) {
 
 int64_t list_scratch_bytes(int64_t capacity) { return list_scratch_words(capacity) * 4; }
 
-void launch_list_active(const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch, int32_t* out,
-                        int64_t out_cap, long long* count_out, const Launch& L) {
+// Listing of a map whose heap's free part is the identity: the live indices
+// are exactly 0..t-1 (the complement of h[t..c) = t..c-1), written in order
+// with 16-byte stores, and the count is t.
+__global__ void list_prefix_kernel(Ctrl* __restrict__ ctrl, int32_t* __restrict__ out, int64_t out_cap,
+                                   long long* count_out) {
+  const int64_t t = static_cast<int64_t>(static_cast<uint32_t>(ctrl->top_used));
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  if (tid == 0) {
+    ctrl->count = static_cast<unsigned long long>(t);
+    if (count_out) *count_out = static_cast<long long>(t);
+  }
+  const int64_t n = min(t, out_cap);
+  const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const int64_t n4 = vec ? n / 4 : 0;
+  for (int64_t q = tid; q < n4; q += stride) {
+    const int32_t v = static_cast<int32_t>(4 * q);
+    reinterpret_cast<int4*>(out)[q] = make_int4(v, v + 1, v + 2, v + 3);
+  }
+  for (int64_t j = 4 * n4 + tid; j < n; j += stride) out[j] = static_cast<int32_t>(j);
+}
+
+void launch_list_active(bool heap_identity, const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch,
+                        int32_t* out, int64_t out_cap, long long* count_out, const Launch& L) {
+  if (heap_identity) {
+    TraceScope ts(kKListActive, L.stream);
+    const int64_t n = std::min(capacity, out_cap);
+    list_prefix_kernel<<<grid_for((n + 3) / 4, L), L.block, 0, L.stream>>>(ctrl, out, out_cap, count_out);
+    return;
+  }
   const int64_t words = list_scratch_words(capacity);
   const int n_blocks = static_cast<int>(words / kListWordsPerBlock);
   uint32_t* bitmap = static_cast<uint32_t*>(scratch);  // all zero between listings

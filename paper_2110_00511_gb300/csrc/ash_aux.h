@@ -15,9 +15,11 @@ struct Launch;
 // memory.  Writes at most out_cap indices; the live count goes to ctrl->count.
 int64_t list_scratch_bytes(int64_t capacity);
 // count_out (optional): device int64 receiving the live count.  The scratch
-// bitmap must be zero on entry; the listing leaves it zero.
-void launch_list_active(const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch, int32_t* out,
-                        int64_t out_cap, long long* count_out, const Launch& L);
+// bitmap must be zero on entry; the listing leaves it zero.  heap_identity:
+// the heap's free part is h[j] = j (no erase since create, clear or a
+// compacting rehash), so the live indices are 0..t-1 and are written directly.
+void launch_list_active(bool heap_identity, const int32_t* heap, int64_t capacity, Ctrl* ctrl, void* scratch,
+                        int32_t* out, int64_t out_cap, long long* count_out, const Launch& L);
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L);
 void launch_set_used_from_count(Ctrl* ctrl, const Launch& L);
 void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);

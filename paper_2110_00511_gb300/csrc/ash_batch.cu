@@ -418,6 +418,8 @@ ash_status ash_batch_run(ash_batch* b, const ash_batch_op* ops, int n_ops, ash_s
     if (ops[i].op == ASH_OP_INSERT || ops[i].op == ASH_OP_ACTIVATE) {
       ops[i].map->pref_placed = false;  // keys placed in slot order
       maybe_snapshot(ops[i].map, st);
+    } else if (ops[i].op == ASH_OP_ERASE) {
+      ops[i].map->heap_identity = false;
     }
   if (cudaEventRecord(sl.done, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventRecord");
   sl.used = true;

@@ -66,8 +66,13 @@ struct TableView {
   uint32_t n_buckets;
   uint32_t max_probes;
   int32_t capacity;
-  int32_t pad;
+  int32_t flags;        // kViewHeapIdentity
 };
+
+// TableView::flags: the free part of the heap is the identity (h[j] = j for
+// j >= t), as it is from create or clear until the first erase.  Commit then
+// takes index t + rank without reading h.
+constexpr int32_t kViewHeapIdentity = 1;
 
 constexpr int kMaxValues = 8;
 

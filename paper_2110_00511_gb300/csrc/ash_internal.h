@@ -65,6 +65,11 @@ struct ash_map {
   // preferred slot blindly.  Set by create, clear and every table rebuild;
   // cleared by batched inserts, which place keys in slot order.
   bool pref_placed = true;
+  // The free part of the heap is the identity (h[j] = j for j >= t), so the
+  // live indices are exactly 0..t-1: true from create, clear or a compacting
+  // rehash until the first erase (growth keeps it).  Commit skips the heap
+  // read and the listing writes 0..t-1.
+  bool heap_identity = true;
   ash_tuning tuning{};
   ash::DimKernels K{};
   ash::host::Allocator alloc;

@@ -684,7 +684,7 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, 
     if (pos < n) {
       if (win[q]) {
         if (r < got) {
-          const int32_t i = t.heap[hbase + r];
+          const int32_t i = (t.flags & kViewHeapIdentity) ? hbase + r : t.heap[hbase + r];
           int32_t k[D];
           load_input_key<D>(keys, pos, k);
           store_kb<D>(t.kb, static_cast<uint32_t>(i), k);

@@ -193,7 +193,7 @@ ash::TableView view_of(const ash_map* m) {
                      ? static_cast<uint32_t>(m->tuning.max_probes)
                      : m->n_buckets;
   t.capacity = static_cast<int32_t>(m->capacity);
-  t.pad = 0;
+  t.flags = m->heap_identity ? ash::kViewHeapIdentity : 0;
   return t;
 }
 
@@ -331,6 +331,7 @@ ash_status alloc_storage(ash_map* m, int64_t capacity, cudaStream_t st) {
   m->S = m->tuning.slots_per_bucket;
   m->n_buckets = static_cast<uint32_t>(n_slots / m->S);
   m->pref_placed = true;
+  m->heap_identity = true;
   ASH_CUDA(cudaMemsetAsync(m->slots, 0xFF, n_slots * 8, st));
   for (int j = 0; j < m->n_values; ++j) ASH_CUDA(cudaMemsetAsync(m->vb[j], 0, capacity * m->row_bytes[j], st));
   ash::launch_iota(m->heap, 0, capacity, L);
@@ -387,7 +388,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
     dev_free(m, list, st);
     return s;
   }
-  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, list, size, nullptr, L);
+  ash::launch_list_active(m->heap_identity, m->heap, m->capacity, m->ctrl, m->list_scratch, list, size, nullptr, L);
   s = check_launch("rehash listing");
   if (s != ASH_OK) return s;
 
@@ -435,6 +436,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
     } else {
       // compaction: entry j of the list becomes index j
       ash::launch_iota(heap, 0, new_capacity, L);
+      m->heap_identity = true;
       ash::ValueCopy vc{};
       vc.n = m->n_values;
       for (int j = 0; j < m->n_values; ++j) {
@@ -491,7 +493,7 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
     dev_free(m, list, st);
     return s;
   }
-  ash::launch_list_active(m->heap, c, m->ctrl, m->list_scratch, list, c, nullptr, L);
+  ash::launch_list_active(m->heap_identity, m->heap, c, m->ctrl, m->list_scratch, list, c, nullptr, L);
   const int64_t n_slots = slots_for(new_capacity, m->tuning);
   if (n_slots >= (int64_t{1} << 31)) {
     dev_free(m, list, st);
@@ -831,6 +833,7 @@ ash_status ash_erase(ash_map* m, const int32_t* keys, int64_t n, uint8_t* masks,
   const ash::TableView tv = view_of(m);
   m->K.erase_mark(m->S, tv, keys, n, m->scratch, L);
   ash::launch_erase_resolve(m->S, tv, n, m->scratch, masks, L);
+  m->heap_identity = false;
   return check_launch("erase");
 }
 
@@ -843,7 +846,7 @@ ash_status ash_get_active_indices(ash_map* m, int32_t* out, int64_t out_capacity
   m->last_stream = st;
   ash_status s = ensure_list_scratch(m, st);
   if (s != ASH_OK) return s;
-  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
+  ash::launch_list_active(m->heap_identity, m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
                           nullptr, launch_of(m, st));
   s = check_launch("get_active_indices");
   if (s != ASH_OK) return s;
@@ -864,7 +867,7 @@ ash_status ash_get_active_indices_async(ash_map* m, int32_t* out, int64_t out_ca
   ash_status s = ensure_list_scratch(m, st);
   if (s != ASH_OK) return s;
   const ash::Launch L = launch_of(m, st);
-  ash::launch_list_active(m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
+  ash::launch_list_active(m->heap_identity, m->heap, m->capacity, m->ctrl, m->list_scratch, out, std::max<int64_t>(out_capacity, 0),
                           reinterpret_cast<long long*>(count_dev), L);
   return check_launch("get_active_indices_async");
 }
@@ -955,6 +958,7 @@ ash_status ash_clear(ash_map* m, ash_stream stream) {
   m->size_ub = 0;
   m->used_ub = 0;
   m->pref_placed = true;
+  m->heap_identity = true;
   invalidate_snapshot(m);
   return check_launch("clear");
 }
@@ -1200,5 +1204,6 @@ extern "C" ash_status ash_erase_noalloc(ash_map* m, const int32_t* keys, int64_t
   const ash::TableView tv = view_of(m);
   m->K.erase_mark(m->S, tv, keys, n, scratch, L);
   ash::launch_erase_resolve(m->S, tv, n, scratch, masks, L);
+  m->heap_identity = false;
   return check_launch("erase_noalloc");
 }
