@@ -93,15 +93,13 @@ typedef struct ash_tuning {
                                    keys_per_thread (the find's dependent reads favour one key per
                                    thread and full occupancy on mid-sized tables) */
   int32_t claim_mode;         /* insert/activate claim protocol: 1 = load the home bucket, then CAS
-                                 an EMPTY slot (the key's preferred slot when it is EMPTY);
-                                 2 = CAS the key's preferred slot first with no load before it,
-                                 keys that find it taken are claimed from their buckets in dense
-                                 warp rounds; 0 = 2 while the table takes at most two thirds
-                                 of L2, else 1 (a CAS that misses L2 waits on DRAM).  Both
-                                 place a key in its preferred slot when that slot is EMPTY, so
-                                 the modes may be switched between calls.  A batched insert
-                                 (ash_batch_run) places keys in slot order; the map then uses 1
-                                 until its next clear or rebuild */
+                                 its first EMPTY slot; 2 = CAS the key's preferred slot of its
+                                 home bucket with no load before it, keys that find it taken are
+                                 claimed from their buckets in dense warp rounds; 0 = 2 while the
+                                 table takes at most two thirds of L2, else 1 (a CAS that misses
+                                 L2 waits on DRAM).  2 needs every key placed preferred-first:
+                                 after a call that ran 1, or a batched insert (ash_batch_run),
+                                 the map uses 1 until its next clear or rebuild */
 } ash_tuning;
 
 /* Fills *out with the defaults. */

@@ -95,7 +95,7 @@ template <int D, int S>
 __device__ __forceinline__ void batch_claim_one(const BatchOp& op, int64_t pos) {
   // slot order (measured 7 % faster here than preferred-first placement);
   // the host clears the map's pref_placed flag
-  op.idx[pos] = claim_key<D, S, const int32_t*, false>(op.t, op.keys, pos);
+  op.idx[pos] = claim_key<D, S, const int32_t*, kClaimSlotMask, false>(op.t, op.keys, pos);
 }
 
 template <int D, int S>

@@ -67,6 +67,12 @@ struct TableView {
   uint32_t max_probes;
   int32_t capacity;
   int32_t flags;        // kViewHeapIdentity
+  // Winner flags of one insert (one bit per input position, zero before the
+  // claim kernel), or null.  A position that displaces an equal key's claim
+  // with a lower position sets the displaced position's bit, so after the
+  // claim kernel a position holding a slot index wins unless its bit is set,
+  // and the commit decides without reading the slot word.
+  uint32_t* lost;
 };
 
 // TableView::flags: the free part of the heap is the identity (h[j] = j for

@@ -43,6 +43,8 @@ struct ash_map {
   ash::Ctrl* ctrl_host = nullptr;  // pinned mirror for synchronising reads
   int32_t* scratch = nullptr;      // erase: one slot index per key
   int64_t scratch_bytes = 0;
+  uint32_t* win_bits = nullptr;    // insert: winner flags, one bit per key
+  int64_t win_bits_bytes = 0;
   void* list_scratch = nullptr;    // listing: free-index bitmap + block counts
   int64_t list_scratch_bytes = 0;
   int64_t size_ub = 0;  // upper bound of live entries since the last sync

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(256) find_group_kernel(TableView t, const int3
 // ------------------------------------------------------------- insert: claim
 // Result codes written to buf_indices[p] by the claim kernel.
 constexpr int32_t kClaimExists = -2;  // key already committed
+constexpr int32_t kClaimJoined = -3;  // an equal key of this batch with a lower position holds the claim
 constexpr int32_t kClaimFailed = -1;  // no slot within max_probes
 
 // 0: no match.  1: slot claimed by an equal key in this batch.  2: committed equal key.
@@ -277,13 +278,52 @@ __device__ __forceinline__ int claim_match(uint64_t w, uint32_t fp, const int32_
   return kb_equal<D>(kb, lo, k) ? 2 : 0;
 }
 
+// This position meets an equal key's claim, with position seen_lo, at slot p:
+// the lower position keeps the claim (atomicMin on the word, whose high half
+// is the shared fingerprint).  Returns false when this position lost for
+// sure (a lower one holds the claim); true when it holds the claim for now.
+// With winner flags (FLAGS and t.lost) the position it displaced is marked
+// lost.
+template <bool FLAGS = true>
+__device__ __forceinline__ bool join_claim(const TableView& t, uint64_t* p, uint32_t seen_lo, uint64_t mine,
+                                           uint32_t pos) {
+  if (!FLAGS) {
+    // no winner flags: the commit reads the slot word to see who won
+    if ((seen_lo & ~kClaimBit) > pos)
+      atomicMin(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(mine));
+    return true;
+  }
+  if ((seen_lo & ~kClaimBit) < pos) return false;
+  if (!t.lost) {
+    atomicMin(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(mine));
+    return true;
+  }
+  const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(mine));
+  const uint32_t op = lo32(old) & ~kClaimBit;
+  if (op < pos) return false;
+  atomicOr(t.lost + (op >> 5), 1u << (op & 31));
+  return true;
+}
+
+// Order of the EMPTY slots a claim tries (claim_key):
+//   kClaimSlotOrder  slot order, one CAS site per slot (unrolled): the
+//                    fastest form, used out of line as a slow path
+//   kClaimSlotMask   slot order, one CAS site for all slots (a bit-mask
+//                    loop): fewer registers, for the batched kernel that
+//                    inlines the protocol for every key dimension
+//   kClaimPrefFirst  the key's preferred slot first in its home bucket, then
+//                    slot order (keeps the preferred-slot invariant)
+constexpr int kClaimSlotOrder = 0;
+constexpr int kClaimSlotMask = 1;
+constexpr int kClaimPrefFirst = 2;
+
 // The full claim protocol for one key, from its home bucket: 1) any slot of
 // the bucket holding an equal key ends the search; 2) otherwise the EMPTY
-// slots are claimed in order (PrefFirst: the preferred one first in the home
-// bucket, which keeps the preferred-slot invariant), and a lost CAS re-checks
-// the winner's word for an equal key; 3) a bucket without EMPTY slots sends
-// the key to the next bucket.
-template <int D, int S, class In, bool PrefFirst = true>
+// slots are claimed in the order ORDER gives, and a lost CAS re-checks the
+// winner's word for an equal key; 3) a bucket without EMPTY slots sends the
+// key to the next bucket.  FLAGS: winner flags may be set (t.lost); the
+// batched kernel, which has none, compiles without them.
+template <int D, int S, class In, int ORDER, bool FLAGS = true>
 __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys, int64_t pos) {
   int32_t k[D];
   load_input_key<D>(keys, pos, k);
@@ -299,29 +339,41 @@ __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys,
     for (int s = 0; s < S; ++s) {
       const int m = claim_match<D, In>(w[s], fp, k, keys, t.kb);
       if (m == 2) return kClaimExists;
-      if (m == 1) {
-        if ((lo32(w[s]) & ~kClaimBit) > static_cast<uint32_t>(pos))
-          atomicMin(reinterpret_cast<unsigned long long*>(bp + s), static_cast<unsigned long long>(mine));
-        return static_cast<int32_t>(b * S + s);
-      }
+      if (m == 1)
+        return join_claim<FLAGS>(t, bp + s, lo32(w[s]), mine, static_cast<uint32_t>(pos)) ? static_cast<int32_t>(b * S + s)
+                                                                                    : kClaimJoined;
     }
-    // EMPTY slots of the snapshot as a bit mask (one CAS site for all)
-    uint32_t emask = 0;
+    if constexpr (ORDER == kClaimSlotOrder) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) emask |= (w[s] == kEmpty ? 1u : 0u) << s;
-    const uint32_t pbit = PrefFirst && probe == 0 ? 1u << pref_slot<S>(fp) : 0u;
-    while (emask) {
-      const int s = (emask & pbit) ? static_cast<int>(pref_slot<S>(fp)) : __ffs(emask) - 1;
-      emask &= ~(1u << s);
-      const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(bp + s),
-                                     static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
-      if (old == kEmpty) return static_cast<int32_t>(b * S + s);
-      const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
-      if (m == 2) return kClaimExists;
-      if (m == 1) {
-        if ((lo32(old) & ~kClaimBit) > static_cast<uint32_t>(pos))
-          atomicMin(reinterpret_cast<unsigned long long*>(bp + s), static_cast<unsigned long long>(mine));
-        return static_cast<int32_t>(b * S + s);
+      for (int s = 0; s < S; ++s) {
+        if (w[s] == kEmpty) {
+          const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(bp + s),
+                                         static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+          if (old == kEmpty) return static_cast<int32_t>(b * S + s);
+          const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
+          if (m == 2) return kClaimExists;
+          if (m == 1)
+            return join_claim<FLAGS>(t, bp + s, lo32(old), mine, static_cast<uint32_t>(pos)) ? static_cast<int32_t>(b * S + s)
+                                                                                      : kClaimJoined;
+        }
+      }
+    } else {
+      // EMPTY slots of the snapshot as a bit mask (one CAS site for all)
+      uint32_t emask = 0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) emask |= (w[s] == kEmpty ? 1u : 0u) << s;
+      const uint32_t pbit = ORDER == kClaimPrefFirst && probe == 0 ? 1u << pref_slot<S>(fp) : 0u;
+      while (emask) {
+        const int s = (emask & pbit) ? static_cast<int>(pref_slot<S>(fp)) : __ffs(emask) - 1;
+        emask &= ~(1u << s);
+        const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(bp + s),
+                                       static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(mine));
+        if (old == kEmpty) return static_cast<int32_t>(b * S + s);
+        const int m = claim_match<D, In>(old, fp, k, keys, t.kb);
+        if (m == 2) return kClaimExists;
+        if (m == 1)
+          return join_claim<FLAGS>(t, bp + s, lo32(old), mine, static_cast<uint32_t>(pos)) ? static_cast<int32_t>(b * S + s)
+                                                                                    : kClaimJoined;
       }
     }
     b = next_bucket(b, t.n_buckets);
@@ -332,19 +384,20 @@ __device__ __forceinline__ int32_t claim_key(const TableView& t, const In& keys,
 
 // Out-of-line copy of the full protocol: the rare slow path of the claim
 // kernels (kept out of line so it does not raise their register count).
-template <int D, int S, class In>
+template <int D, int S, class In, bool PrefFirst>
 __device__ __noinline__ int32_t claim_one(const TableView t, const In keys, int64_t pos) {
-  return claim_key<D, S, In>(t, keys, pos);
+  return claim_key<D, S, In, PrefFirst ? kClaimPrefFirst : kClaimSlotOrder>(t, keys, pos);
 }
 
 // Claim from the loaded home bucket, DK keys per lane (pos[q] valid where
-// v[q]).  Per key: if the bucket holds exactly one slot with the key's
-// fingerprint, compare once (claimant's input row or kB row); on no match,
-// CAS the preferred slot if it is EMPTY, else the first EMPTY slot.
-// The loads, compares and CASes of the DK keys are issued back to back.
-// Anything else (several fingerprint matches, a lost CAS, a full bucket) runs
-// claim_one, which is safe because this path changed nothing then.
-template <int D, int S, int DK, class In>
+// v[q]; an invalid lane hashes key 0 and loads that bucket, in bounds).  Per
+// key: if the bucket holds exactly one slot with the key's fingerprint,
+// compare once (claimant's input row or kB row); on no match, CAS the first
+// EMPTY slot (PrefFirst: the preferred slot when it is EMPTY).  The loads,
+// compares and CASes of the DK keys are issued back to back.  Anything else
+// (several fingerprint matches, a lost CAS, a full bucket) runs claim_one,
+// which is safe because this path changed nothing then.
+template <int D, int S, int DK, class In, bool PrefFirst>
 __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& keys, const int64_t (&pos)[DK],
                                                   const bool (&v)[DK], int32_t* __restrict__ slot_out) {
   constexpr int KS = KeyStride<D>::value;
@@ -364,14 +417,7 @@ __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& 
   }
   uint64_t w[DK][S];
 #pragma unroll
-  for (int q = 0; q < DK; ++q) {
-    if (v[q]) {
-      load_bucket<S, false>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
-    } else {
-#pragma unroll
-      for (int s = 0; s < S; ++s) w[q][s] = kTombstone;
-    }
-  }
+  for (int q = 0; q < DK; ++q) load_bucket<S, false>(t.slots + static_cast<size_t>(b[q]) * S, w[q]);
   int cs[DK], nc[DK], es[DK];
   uint32_t clo[DK];
 #pragma unroll
@@ -391,9 +437,9 @@ __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& 
       }
       nc[q] += m ? 1 : 0;
       if (es[q] < 0 && w[q][s] == kEmpty) es[q] = s;
-      if (static_cast<uint32_t>(s) == pref && w[q][s] == kEmpty) pe = s;
+      if (PrefFirst && static_cast<uint32_t>(s) == pref && w[q][s] == kEmpty) pe = s;
     }
-    if (pe >= 0) es[q] = pe;  // preferred slot first (preferred-slot invariant)
+    if (PrefFirst && pe >= 0) es[q] = pe;  // preferred slot first (preferred-slot invariant)
   }
   int32_t row[DK][KS];
 #pragma unroll
@@ -425,12 +471,11 @@ __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& 
       for (int j = 0; j < D; ++j) eq &= (row[q][j] == k[q][j]);
       if (eq) {
         if (clo[q] & kClaimBit) {
-          if ((clo[q] & ~kClaimBit) > static_cast<uint32_t>(pos[q])) {
-            const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos[q]));
-            atomicMin(reinterpret_cast<unsigned long long*>(t.slots + static_cast<size_t>(b[q]) * S + cs[q]),
-                      static_cast<unsigned long long>(mine));
-          }
-          res[q] = static_cast<int32_t>(b[q] * S + cs[q]);
+          const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos[q]));
+          res[q] = join_claim(t, t.slots + static_cast<size_t>(b[q]) * S + cs[q], clo[q], mine,
+                              static_cast<uint32_t>(pos[q]))
+                       ? static_cast<int32_t>(b[q] * S + cs[q])
+                       : kClaimJoined;
         } else {
           res[q] = kClaimExists;
         }
@@ -457,15 +502,17 @@ __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& 
       if (old[q] == kEmpty) res[q] = static_cast<int32_t>(b[q] * S + es[q]);
       else slow[q] = true;
     }
-    if (slow[q]) res[q] = claim_one<D, S, In>(t, keys, pos[q]);  // rare
+    if (slow[q]) res[q] = claim_one<D, S, In, PrefFirst>(t, keys, pos[q]);  // rare
     if (v[q]) slot_out[pos[q]] = res[q];
   }
 }
 
 // Claim kernel, bucket load first: KPT keys per thread, each claimed from its
-// loaded home bucket (two dependent accesses per key: bucket load, CAS).  The
-// better choice when the table does not stay in L2: the loads bring the
-// buckets in with deep miss queues and the CASes then hit L2.
+// loaded home bucket (two dependent accesses per key: bucket load, CAS) in
+// slot order.  The better choice when the table does not stay in L2: the
+// loads bring the buckets in with deep miss queues and the CASes then hit L2.
+// Slot order does not keep the preferred-slot invariant (preferred-first
+// placement measured 5-10 % slower here), so the host clears the map's flag.
 template <int D, int S, int KPT, class In = const int32_t*>
 __global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In keys, int64_t n,
                                                            int32_t* __restrict__ slot_out) {
@@ -478,7 +525,7 @@ __global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In
       p[q] = base + static_cast<int64_t>(q) * blockDim.x;
       v[q] = p[q] < n;
     }
-    claim_from_bucket<D, S, KPT, In>(t, keys, p, v, slot_out);
+    claim_from_bucket<D, S, KPT, In, false>(t, keys, p, v, slot_out);
   }
 }
 
@@ -568,11 +615,10 @@ __global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In k
         } else if (!eq) {
           pending = true;
         } else if (lo & kClaimBit) {
-          if ((lo & ~kClaimBit) > static_cast<uint32_t>(pos)) {
-            const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
-            atomicMin(reinterpret_cast<unsigned long long*>(t.slots + ps[q]), static_cast<unsigned long long>(mine));
-          }
-          slot_out[pos] = static_cast<int32_t>(ps[q]);
+          const uint64_t mine = (static_cast<uint64_t>(fp[q]) << 32) | (kClaimBit | static_cast<uint32_t>(pos));
+          slot_out[pos] = join_claim(t, t.slots + ps[q], lo, mine, static_cast<uint32_t>(pos))
+                              ? static_cast<int32_t>(ps[q])
+                              : kClaimJoined;
         } else {
           slot_out[pos] = kClaimExists;
         }
@@ -592,7 +638,7 @@ __global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In k
       }
       __syncwarp();
       qn -= kDrain;
-      claim_from_bucket<D, S, 2, In>(t, keys, p, v, slot_out);
+      claim_from_bucket<D, S, 2, In, true>(t, keys, p, v, slot_out);
     }
   }
   __syncwarp();
@@ -604,7 +650,7 @@ __global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In k
       v[r] = r * 32 + lane < qn;
       p[r] = v[r] ? queue[r * 32 + lane] : 0;
     }
-    claim_from_bucket<D, S, 2, In>(t, keys, p, v, slot_out);
+    claim_from_bucket<D, S, 2, In, true>(t, keys, p, v, slot_out);
   }
 }
 
@@ -628,12 +674,14 @@ __device__ __forceinline__ void copy_small_row(const ValueRow& v, int32_t i, int
   else *reinterpret_cast<uint32_t*>(d) = __ldg(reinterpret_cast<const uint32_t*>(s));
 }
 
-// KPT keys per thread per block iteration (blockDim.x * KPT keys): the slot
-// index and slot word of every key are loaded first (independent loads), one
-// block-wide scan ranks the winners and ONE heap atomic serves the iteration
-// (Sec. 4.3: t is raised by the number of indices taken).  Winners then write
-// kB(i), the value row, the committed slot word and their outputs.
-template <int D, int KPT, bool VAL, class In>
+// KPT keys per thread per block iteration (blockDim.x * KPT keys).  Who won
+// each key: FLAGS, a position holding a slot index whose winner-flag bit
+// (t.lost) is clear, from two streamed reads; otherwise the slot word, read
+// at random, names the winning position.  One block-wide scan ranks the
+// winners and ONE heap atomic serves the iteration (Sec. 4.3: t is raised by
+// the number of indices taken).  Winners then write kB(i), the value row, the
+// committed slot word and their outputs.
+template <int D, int KPT, bool VAL, class In, bool FLAGS = false>
 __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, int64_t n,
                                             int64_t base0, int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
                                             const ValueRow& v, int* s_warp, int* s_base, int* s_got) {
@@ -645,15 +693,31 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, 
     s[q] = pos < n ? idx[pos] : -1;
   }
   uint64_t w[KPT];
-#pragma unroll
-  for (int q = 0; q < KPT; ++q) w[q] = s[q] >= 0 ? load_slot_relaxed(t.slots + s[q]) : 0ull;
   bool win[KPT];
   int cnt = 0;
+  if constexpr (FLAGS) {
+    uint32_t lw[KPT];
 #pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
-    win[q] = s[q] >= 0 && lo32(w[q]) == (kClaimBit | static_cast<uint32_t>(pos));
-    cnt += win[q] ? 1 : 0;
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      lw[q] = pos < n ? t.lost[pos >> 5] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      w[q] = 0;
+      win[q] = s[q] >= 0 && !((lw[q] >> (pos & 31)) & 1u);
+      cnt += win[q] ? 1 : 0;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) w[q] = s[q] >= 0 ? load_slot_relaxed(t.slots + s[q]) : 0ull;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      win[q] = s[q] >= 0 && lo32(w[q]) == (kClaimBit | static_cast<uint32_t>(pos));
+      cnt += win[q] ? 1 : 0;
+    }
   }
   int total;
   const int off = block_exclusive_scan(cnt, total, s_warp);
@@ -689,7 +753,8 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, 
           load_input_key<D>(keys, pos, k);
           store_kb<D>(t.kb, static_cast<uint32_t>(i), k);
           if constexpr (VAL) copy_small_row(v, i, pos);
-          t.slots[s[q]] = (static_cast<uint64_t>(hi32(w[q])) << 32) | static_cast<uint32_t>(i);
+          const uint32_t fp = FLAGS ? fingerprint(hash_key<D>(k)) : hi32(w[q]);
+          t.slots[s[q]] = (static_cast<uint64_t>(fp) << 32) | static_cast<uint32_t>(i);
           idx[pos] = i;
           mask[pos] = 1;
         } else {
@@ -707,7 +772,7 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, 
   __syncthreads();
 }
 
-template <int D, int KPT, bool VAL, class In = const int32_t*>
+template <int D, int KPT, bool VAL, class In = const int32_t*, bool FLAGS = false>
 __global__ void __launch_bounds__(256) commit_kernel(TableView t, const In keys, int64_t n,
                                                      int32_t* __restrict__ idx, uint8_t* __restrict__ mask,
                                                      ValueRow v) {
@@ -716,7 +781,7 @@ __global__ void __launch_bounds__(256) commit_kernel(TableView t, const In keys,
   __shared__ int s_got;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step)
-    commit_tile<D, KPT, VAL, In>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
+    commit_tile<D, KPT, VAL, In, FLAGS>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
 }
 
 // --------------------------------------------------------------- erase: mark
@@ -978,8 +1043,9 @@ struct DimLaunchers {
   static void commit_kv(const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
                         const ValueRow& v, const Launch& L) {
     TraceScope ts(kKCommit, L.stream);
-    commit_kernel<D, KPT, VAL, In>
-        <<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
+    const int g = grid_for((n + KPT - 1) / KPT, L);
+    if (t.lost) commit_kernel<D, KPT, VAL, In, true><<<g, L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
+    else commit_kernel<D, KPT, VAL, In, false><<<g, L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
   }
   template <bool VAL, class In>
   static void commit_v(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,

@@ -167,7 +167,7 @@ ash::DimKernels kernels_for(int d) {
 // atomic unit), else the bucket load first.  On GB300 (L2 135.5 MB) the
 // preferred-slot path is 6-25 % faster up to 80 MB tables, even at 96 MB and
 // 19 % slower at 128 MB.  It needs the preferred-slot invariant, which a
-// batched insert gives up until the next clear or rebuild.
+// bucket-first or batched insert gives up until the next clear or rebuild.
 int claim_prefers_slot(const ash_map* m) {
   if (m->tuning.claim_mode == 1 || !m->pref_placed) return 0;
   if (m->tuning.claim_mode == 2) return 1;
@@ -194,6 +194,7 @@ ash::TableView view_of(const ash_map* m) {
                      : m->n_buckets;
   t.capacity = static_cast<int32_t>(m->capacity);
   t.flags = m->heap_identity ? ash::kViewHeapIdentity : 0;
+  t.lost = nullptr;
   return t;
 }
 
@@ -359,6 +360,21 @@ ash_status ensure_scratch(ash_map* m, int64_t bytes, cudaStream_t st) {
     return fail(ASH_ERR_OOM, "scratch allocation failed");
   }
   m->scratch_bytes = want;
+  return ASH_OK;
+}
+
+// Winner flags of an insert of n keys: one bit per input position.
+ash_status ensure_win_bits(ash_map* m, int64_t n, cudaStream_t st) {
+  const int64_t bytes = (n + 31) / 32 * 4;
+  if (m->win_bits_bytes >= bytes) return ASH_OK;
+  dev_free(m, m->win_bits, st);
+  const int64_t want = std::max<int64_t>(bytes, m->win_bits_bytes * 2);
+  m->win_bits = static_cast<uint32_t*>(dev_alloc(m, want, st));
+  if (!m->win_bits) {
+    m->win_bits_bytes = 0;
+    return fail(ASH_ERR_OOM, "winner-flag allocation failed");
+  }
+  m->win_bits_bytes = want;
   return ASH_OK;
 }
 
@@ -604,12 +620,17 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   m->last_stream = st;
   s = ensure_room(m, n, st);
   if (s != ASH_OK) return s;
+  s = ensure_win_bits(m, n, st);
+  if (s != ASH_OK) return s;
+  ASH_CUDA(cudaMemsetAsync(m->win_bits, 0, (n + 31) / 32 * 4, st));
   const ash::Launch L = launch_of(m, st);
-  const ash::TableView tv = view_of(m);
+  ash::TableView tv = view_of(m);
+  tv.lost = m->win_bits;
   const int kpt = m->tuning.keys_per_thread;
   const int pref = claim_prefers_slot(m);
   if (pts) m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
   else m->K.claim(m->S, kpt, pref, tv, keys, n, idx, L);
+  if (!pref) m->pref_placed = false;  // the bucket-first claim places keys in slot order
   // one value buffer with small rows: copied by the committing thread;
   // anything else: warp-per-row scatter after the commit
   bool inline_value = false;
@@ -744,6 +765,7 @@ ash_status ash_destroy(ash_map* m) {
   cudaStream_t st = m->last_stream;
   free_storage(m, st);
   dev_free(m, m->scratch, st);
+  dev_free(m, m->win_bits, st);
   dev_free(m, m->list_scratch, st);
   dev_free(m, m->ctrl, st);
   pinned_ctrl_give(m->ctrl_host);
