@@ -100,6 +100,9 @@ typedef struct ash_tuning {
                                  L2 waits on DRAM).  2 needs every key placed preferred-first:
                                  after a call that ran 1, or a batched insert (ash_batch_run),
                                  the map uses 1 until its next clear or rebuild */
+  int32_t commit_keys_per_thread; /* keys per thread of the insert commit kernel: 1, 2 or 4, or 0
+                                     to use keys_per_thread (its reads are streamed, so one key
+                                     per thread and full occupancy usually win) */
 } ash_tuning;
 
 /* Fills *out with the defaults. */

@@ -217,6 +217,9 @@ ash_status validate_tuning(const ash_tuning& t) {
       t.find_keys_per_thread != 4)
     return fail(ASH_ERR_INVALID, "find_keys_per_thread must be 0, 1, 2 or 4");
   if (t.claim_mode < 0 || t.claim_mode > 2) return fail(ASH_ERR_INVALID, "claim_mode must be 0, 1 or 2");
+  if (t.commit_keys_per_thread != 0 && t.commit_keys_per_thread != 1 && t.commit_keys_per_thread != 2 &&
+      t.commit_keys_per_thread != 4)
+    return fail(ASH_ERR_INVALID, "commit_keys_per_thread must be 0, 1, 2 or 4");
   return ASH_OK;
 }
 
@@ -655,8 +658,9 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
       }
     }
   }
-  if (pts) m->K.commit_pts(kpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
-  else m->K.commit(kpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+  const int ckpt = m->tuning.commit_keys_per_thread ? m->tuning.commit_keys_per_thread : kpt;
+  if (pts) m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
+  else m->K.commit(ckpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
   if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
   m->size_ub += n;
   m->used_ub += n;
@@ -687,6 +691,7 @@ void ash_default_tuning(ash_tuning* out) {
   out->warp_probe = 0;
   out->find_keys_per_thread = 1;
   out->claim_mode = 0;
+  out->commit_keys_per_thread = 1;
 }
 
 ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {

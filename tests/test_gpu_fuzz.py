@@ -30,6 +30,7 @@ def dev(x):
 @pytest.mark.parametrize("seed", range(60))
 def test_random_sequences(seed):
     rng = np.random.default_rng(7000 + seed)
+    mode_rng_init = np.random.default_rng(9500 + seed)  # knobs drawn apart from the op sequence
     d = int(rng.choice([1, 2, 3, 4, 5, 8]))
     cap = int(rng.integers(1, 300))
     t = ash.default_tuning()
@@ -38,6 +39,7 @@ def test_random_sequences(seed):
     t.keys_per_thread = int(rng.choice([1, 2, 4]))
     t.warp_probe = int(rng.integers(0, 2))
     t.find_keys_per_thread = int(rng.choice([0, 1, 2, 4]))
+    t.commit_keys_per_thread = int(mode_rng_init.choice([0, 1, 2, 4]))
     t.block_threads = int(rng.choice([64, 128, 256]))
     vrow = int(rng.choice([0, 4, 12]))
     shapes, dtypes, rbs = ([], [], []) if vrow == 0 else ([(vrow // 4,)], [torch.float32], [vrow])
