@@ -66,7 +66,7 @@ struct TableView {
   uint32_t n_buckets;
   uint32_t max_probes;
   int32_t capacity;
-  int32_t flags;        // kViewHeapIdentity
+  int32_t flags;        // kViewHeapIdentity | kViewPrefPlaced
   // Winner flags of one insert (one bit per input position, zero before the
   // claim kernel), or null.  A position that displaces an equal key's claim
   // with a lower position sets the displaced position's bit, so after the
@@ -79,6 +79,11 @@ struct TableView {
 // j >= t), as it is from create or clear until the first erase.  Commit then
 // takes index t + rank without reading h.
 constexpr int32_t kViewHeapIdentity = 1;
+// TableView::flags: the map keeps the preferred-slot invariant (no bucket-
+// first or batched insert since create, clear or the last rebuild).  Erase
+// must then keep it too; otherwise it may empty any slot of a bucket that
+// has an EMPTY slot.
+constexpr int32_t kViewPrefPlaced = 2;
 
 constexpr int kMaxValues = 8;
 

@@ -843,10 +843,11 @@ __device__ __forceinline__ void erase_resolve_tile(const TableView& t, int64_t n
     win = hi32(w) == static_cast<uint32_t>(pos);
     if (win) {
       // EMPTY only when the bucket already has an EMPTY slot (no probe chain
-      // passes through it) and no other live key of the bucket prefers the
-      // freed slot (the preferred-slot invariant); a TOMBSTONE otherwise.
-      // (the freed slot itself holds a marked word, which never counts).  The
-      // bucket is read 32 bytes at a time to keep few words live.
+      // passes through it) and, while the map keeps the preferred-slot
+      // invariant, no other live key of the bucket prefers the freed slot; a
+      // TOMBSTONE otherwise (the freed slot itself holds a marked word, which
+      // never counts).  The bucket is read 32 bytes at a time to keep few
+      // words live.
       const uint64_t* bp = t.slots + static_cast<size_t>(s / S) * S;
       const uint32_t own = static_cast<uint32_t>(s) & (S - 1);
       bool preferred = false;
@@ -860,7 +861,7 @@ __device__ __forceinline__ void erase_resolve_tile(const TableView& t, int64_t n
           preferred |= is_committed(cw[j]) && pref_slot<S>(hi32(cw[j])) == own;
         }
       }
-      to_empty &= !preferred;
+      to_empty &= !(preferred && (t.flags & kViewPrefPlaced));
     }
   }
   int rank, total;
@@ -950,7 +951,33 @@ struct Launch {
   cudaStream_t stream;
   int grid_cap;  // SMs x blocks_per_sm
   int block;
+  int sms = 0;   // SM count (0: unknown)
 };
+
+// Blocks of `kernel` (block threads `block`, no dynamic shared memory) that
+// fit on one SM, from the occupancy API, cached per kernel and block size.
+template <class K>
+inline int resident_blocks(K kernel, int block) {
+  static int cache[9] = {};  // block / 32 in 1..8
+  const int slot = block / 32;
+  if (slot < 1 || slot > 8) return 1;
+  if (cache[slot] == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
+    cache[slot] = nb;
+  }
+  return cache[slot];
+}
+
+// Grid of a grid-stride kernel whose registers allow fewer resident blocks
+// than the Launch's cap: no more blocks than fit at once, so no thin second
+// wave runs at low occupancy.
+template <class K>
+inline int resident_grid(K kernel, int want, const Launch& L) {
+  if (L.sms <= 0) return want;
+  const int cap = L.sms * resident_blocks(kernel, L.block);
+  return want < cap ? want : cap;
+}
 
 inline int grid_for(int64_t n, const Launch& L) {
   int64_t g = (n + L.block - 1) / L.block;
@@ -1014,8 +1041,13 @@ struct DimLaunchers {
                        const Launch& L) {
     TraceScope ts(kKClaim, L.stream);
     const int g = grid_for((n + KPT - 1) / KPT, L);
-    if (pref) claim_pref_kernel<D, S, KPT, In><<<g, L.block, 0, L.stream>>>(t, keys, n, slot_out);
-    else claim_bucket_kernel<D, S, KPT, In><<<g, L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    if (pref) {
+      auto* k = claim_pref_kernel<D, S, KPT, In>;
+      k<<<resident_grid(k, g, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    } else {
+      auto* k = claim_bucket_kernel<D, S, KPT, In>;
+      k<<<resident_grid(k, g, L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+    }
   }
   template <int S, class In>
   static void claim_s(int kpt, int pref, const TableView& t, const In& keys, int64_t n, int32_t* slot_out,

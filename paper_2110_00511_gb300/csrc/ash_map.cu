@@ -179,6 +179,7 @@ ash::Launch launch_of(const ash_map* m, cudaStream_t st) {
   L.stream = st;
   L.block = m->tuning.block_threads;
   L.grid_cap = sm_count(m->device) * m->tuning.blocks_per_sm;
+  L.sms = sm_count(m->device);
   return L;
 }
 
@@ -193,7 +194,7 @@ ash::TableView view_of(const ash_map* m) {
                      ? static_cast<uint32_t>(m->tuning.max_probes)
                      : m->n_buckets;
   t.capacity = static_cast<int32_t>(m->capacity);
-  t.flags = m->heap_identity ? ash::kViewHeapIdentity : 0;
+  t.flags = (m->heap_identity ? ash::kViewHeapIdentity : 0) | (m->pref_placed ? ash::kViewPrefPlaced : 0);
   t.lost = nullptr;
   return t;
 }
