@@ -186,16 +186,20 @@ def bytes_find(n_hit, n_miss, d=3):
 
 
 def bytes_claim(n, d=3):
-    """Per key: key row in (4d) + bucket sector read and CAS write-back (64) + slot index out (4)."""
+    """Per key: key row in (4d) + one slot sector read and written back (64;
+    the bucket load and CAS of the bucket-first claim, the CAS of the
+    preferred-slot claim) + slot index out (4)."""
     return n * (4 * d + 68)
 
 
-def bytes_commit(n, n_slotted, n_win, value_bytes, d=3):
-    """Per key: slot index in (4) + index and mask out (5); keys holding a slot
-    read it (32); winners read the heap (4) and their key row (4d), write a kB
-    row (4*stride), rewrite the slot sector (32) and copy their value rows
-    (read + write)."""
-    return n * 9 + n_slotted * 32 + n_win * (4 + 4 * d + 4 * key_stride(d) + 32 + 2 * value_bytes)
+def bytes_commit(n, n_win, value_bytes, d=3, heap_identity=True):
+    """Per key: slot index in (4) + index and mask out (5) + its winner-flag
+    bit (1/8); winners read their key row (4d), write a kB row (4*stride),
+    rewrite the slot sector (32) and copy their value rows (read + write),
+    and read the heap (4) unless its free part is the identity (a map with
+    no erase since create, clear or a compacting rehash)."""
+    per_win = 4 * d + 4 * key_stride(d) + 32 + 2 * value_bytes + (0 if heap_identity else 4)
+    return n * 9 + (n + 7) // 8 + n_win * per_win
 
 
 def bytes_list(capacity, n_live, heap_identity=True):
@@ -493,7 +497,7 @@ def main(argv=None):
     per_launch_bytes = {
         "quantize": bytes_quantize(3 * N),
         "insert_claim": bytes_claim(N),
-        "insert_commit": bytes_commit(N, N, n_unique, 4),
+        "insert_commit": bytes_commit(N, n_unique, 4),
         "find": bytes_find(N, 0),
         "list_active": bytes_list(N, n_unique),
         "gather_keys": bytes_gather_keys(n_unique),
@@ -868,7 +872,7 @@ def sweep_figures(args, device, hbm_peak, random_read_gbs):
         t = hm.tuning()
         slots = n * t.slots_per_capacity
         working = int(slots * 8 + n * 16 + n * 12 + n * 5)   # table, kB, keys in, outputs
-        b_act = bytes_claim(n) + bytes_commit(n, n, n_unique, 0)
+        b_act = bytes_claim(n) + bytes_commit(n, n_unique, 0)
         b_find = bytes_find(n, 0)
         rec = {"n": n, "rho": rho, "unique": n_unique, "working_set_x_l2": working / l2}
         for name, ms, nbytes in (("activate", ms_act, b_act), ("find", ms_find, b_find)):
@@ -1102,7 +1106,7 @@ def per_op_figures(args, device, hbm_peak):
         ms_ins.append(e0.elapsed_time(e1))
     hm = state["hm"]
     t = hm.tuning()
-    rec("insert", min(ms_ins), bytes_claim(n) + bytes_commit(n, n, n_unique, 4), n)
+    rec("insert", min(ms_ins), bytes_claim(n) + bytes_commit(n, n_unique, 4), n)
     rec("find_hit", timed(lambda: hm.find(keys)), bytes_find(n, 0), n)
     rec("find_miss", timed(lambda: hm.find(miss)), bytes_find(0, n), n)
     # thread-per-key vs warp-cooperative probing, on 32 B and 128 B buckets
@@ -1133,7 +1137,7 @@ def per_op_figures(args, device, hbm_peak):
         torch.cuda.synchronize()
         ms_act.append(e0.elapsed_time(e1))
         del h2
-    rec("activate", min(ms_act), bytes_claim(n) + bytes_commit(n, n, n_unique, 0), n)
+    rec("activate", min(ms_act), bytes_claim(n) + bytes_commit(n, n_unique, 0), n)
     import math
     n_slots = int(math.ceil(n * t.slots_per_capacity / t.slots_per_bucket)) * t.slots_per_bucket
     rec("list_active", timed(lambda: hm.active_indices()), bytes_list(n, n_unique), n_unique)
