@@ -82,8 +82,10 @@ typedef struct ash_tuning {
                                  this limit, both bases aligned to the row size) has them copied by
                                  the committing thread; other layouts use a warp-per-row scatter
                                  kernel after the commit */
-  int32_t keys_per_thread;    /* 1, 2 or 4 keys handled together by each thread of the find, claim
-                                 and commit kernels (more independent memory requests in flight) */
+  int32_t keys_per_thread;    /* 1, 2 or 4 keys handled together by each thread of the find,
+                                 bucket-first claim and commit kernels (more independent memory
+                                 requests in flight); the preferred-slot claim takes one key per
+                                 thread */
   int32_t warp_probe;         /* find: 0 = one thread per key (keys_per_thread keys each);
                                  1 = warp-cooperative probing, a group of slots_per_bucket / 2 lanes
                                  per key, each lane comparing two slots from one 16-byte load and
