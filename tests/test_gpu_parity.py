@@ -402,6 +402,22 @@ def test_edge_cases():
     assert_heap_permutation(hm)
 
 
+@pytest.mark.parametrize("field,value", [("claim_mode", 3), ("claim_mode", -1), ("commit_keys_per_thread", 3),
+                                         ("keys_per_thread", 0), ("find_keys_per_thread", 5)])
+def test_tuning_validation(field, value):
+    """Out-of-range tuning fields are refused at create and at set_tuning,
+    and a refused set_tuning leaves the map's tuning as it was."""
+    with pytest.raises(ash.AshError) as e:
+        ash.HashMap(3, 64, tuning=tuning(**{field: value}))
+    assert e.value.status == ash.ASH_ERR_INVALID
+    hm = ash.HashMap(3, 64)
+    before = hm.tuning().as_dict()
+    with pytest.raises(ash.AshError) as e:
+        hm.set_tuning(tuning(**{field: value}))
+    assert e.value.status == ash.ASH_ERR_INVALID
+    assert hm.tuning().as_dict() == before
+
+
 def test_capacity_error_without_growth():
     t = tuning(auto_grow=0)
     hm = ash.HashMap(3, 100, tuning=t)
