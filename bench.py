@@ -17,6 +17,7 @@ import datetime
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -232,13 +233,21 @@ def bytes_erase(n_present, n_absent, d=3):
 KERNEL_SOURCES = ("ash_device.cuh", "ash_kernels.cuh", "ash_dim.cu")
 
 
+def _code_only(text):
+    """Source text without comments and whitespace runs: a comment edit
+    does not change the compiled kernels, so it keeps the digest."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_00511_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             h.update(f.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

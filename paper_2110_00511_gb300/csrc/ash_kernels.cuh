@@ -5,30 +5,39 @@
 //                 against kB (Eq. (4)); keys that overflow their home bucket
 //                 take the scalar probe loop.
 // insert/activate two kernels (Sec. 4.3.1 lazy insertion, redesigned):
-//   claim         one thread per input key.  A key already committed is
-//                 rejected.  Otherwise the thread claims the first EMPTY slot
-//                 of its probe sequence with a CAS writing {fingerprint,
-//                 kClaimBit | input position}.  A thread that meets a claimed
-//                 slot compares its key with the READ-ONLY input row of the
-//                 claimant (never with a half-written kB row, which removes the
-//                 torn-copy race of Sec. 4.4.2) and, if equal, lowers the
-//                 recorded position with atomicMin.  After the kernel each
-//                 claimed slot names the lowest input position of its key.
-//                 The slot index goes to buf_indices[p] as scratch.
-//   commit        one thread per input key: the position named by its slot
-//                 wins, takes a buffer index from the heap (one atomicAdd per
-//                 block on t, Sec. 4.3), writes kB(i) and small value rows,
-//                 then replaces the claim with {fingerprint, i}.  Only winners
-//                 allocate ("allocate only on success", Sec. 4.3.1).
+//   claim         a key already committed is rejected.  Otherwise the thread
+//                 claims an EMPTY slot with a CAS writing {fingerprint,
+//                 kClaimBit | input position}: either the key's preferred
+//                 slot of its home bucket, CASed with no load before it
+//                 (claim_pref_kernel, while the table fits in L2; keys that
+//                 find it taken are queued per warp and claimed from their
+//                 buckets in dense rounds), or the first EMPTY slot of the
+//                 loaded home bucket (claim_bucket_kernel).  A thread that
+//                 meets a claimed slot compares its key with the READ-ONLY
+//                 input row of the claimant (never with a half-written kB
+//                 row, which removes the torn-copy race of Sec. 4.4.2) and,
+//                 if equal, lowers the recorded position with atomicMin,
+//                 marking the position it displaced in the winner flags.
+//                 After the kernel each claimed slot names the lowest input
+//                 position of its key.  The slot index goes to
+//                 buf_indices[p] as scratch.
+//   commit        one thread per input key: a position holding a slot index
+//                 whose winner flag is clear wins, takes a buffer index from
+//                 the heap (one atomicAdd per block on t, Sec. 4.3), writes
+//                 kB(i) and small value rows, then replaces the claim with
+//                 {fingerprint, i}.  Only winners allocate ("allocate only on
+//                 success", Sec. 4.3.1).
 // erase           two kernels: mark (atomicMin of the input position into the
 //                 slot's high word, keeping the buffer index) and resolve (the
 //                 lowest position wins, frees the index with one atomic per
 //                 block, and empties the slot, or leaves a tombstone when its
-//                 bucket holds no EMPTY slot).  Allocation and free never run
-//                 in the same kernel (the atomicAdd/atomicSub conflict that
-//                 Sec. 4.3.1 warns about).
+//                 bucket holds no EMPTY slot or, under the preferred-slot
+//                 invariant, another live key prefers it).  Allocation and
+//                 free never run in the same kernel (the atomicAdd/atomicSub
+//                 conflict that Sec. 4.3.1 warns about).
 // rebuild         inserts already-unique keys (rehash, Sec. 4.5) into an empty
-//                 table: first EMPTY slot wins, no key comparisons.
+//                 table: the preferred slot first, else the first EMPTY slot
+//                 of the probe sequence, no key comparisons.
 #pragma once
 
 #include "ash_device.cuh"
