@@ -538,18 +538,18 @@ __global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In
   }
 }
 
-// Claim kernel, preferred slot first.  Each warp takes 32 * KPT consecutive keys per iteration
-// (KPT per lane).  Fast path per key: CAS the preferred slot of the home
-// bucket, with no bucket load before it.  EMPTY there: claimed.  An occupant
-// with the key's fingerprint: compare once (claimant's input row or kB row);
-// an equal key joins the claim (lowest position wins) or reports the
-// committed key.  Any other key (the preferred slot holds another key, a
-// tombstone, or a fingerprint collision) is queued in the warp's shared-memory
-// list; whenever the list holds 64 keys the warp claims them from their
-// buckets together, two per lane (claim_from_bucket), so the slower path runs
-// on dense warps instead of stalling every warp for a few lanes.
-// A CAS that misses L2 waits on DRAM inside the atomic unit, so this path
-// pays off while the table stays in L2.
+// Claim kernel, preferred slot first.  Each warp takes 32 * KPT consecutive
+// keys per iteration (KPT per lane; the launcher uses 1).  Fast path per key:
+// CAS the preferred slot of the home bucket, with no bucket load before it.
+// EMPTY there: claimed.  An occupant with the key's fingerprint: compare once
+// (claimant's input row or kB row); an equal key joins the claim (lowest
+// position wins) or reports the committed key.  Any other key (the preferred
+// slot holds another key, a tombstone, or a fingerprint collision) is queued
+// in the warp's shared-memory list; whenever the list holds 32 * kDL keys the
+// warp claims them from their buckets together, kDL per lane
+// (claim_from_bucket), so the slower path runs on dense warps instead of
+// stalling every warp for a few lanes.  A CAS that misses L2 waits on DRAM
+// inside the atomic unit, so this path pays off while the table stays in L2.
 template <int D, int S, int KPT, class In = const int32_t*>
 __global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In keys, int64_t n,
                                                          int32_t* __restrict__ slot_out) {
