@@ -63,6 +63,9 @@ def parse_args(argv=None):
                    help="override the sweep points, e.g. 20000000:0.5,1000000:1.0")
     p.add_argument("--block-frames", type=int, default=200)
     p.add_argument("--tsdf-frames", type=int, default=40)
+    p.add_argument("--detail", type=str, default=os.path.join(ROOT, "bench_detail.json"),
+                   help="file for the full results (sweep, per-op, batched, serving, TSDF, per-kernel figures); "
+                        "stdout gets one compact summary line")
     return p.parse_args(argv)
 
 
@@ -278,39 +281,32 @@ def peaks():
 
 # ------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, as it stands, over the whole
+    voxelization workload on every host core (keys sharded by hash, one
+    sequential oracle map per thread; see oracle_all_cores_step)."""
     if rank != 0:
         return 0
-    import oracle
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2110_00511_gb300 import workloads
-    sample_n = min(args.points, 1_000_000)
-    pts = workloads.voxel_scene_points(n=args.points, seed=0)[:sample_n]
-    vals = np.arange(sample_n, dtype=np.int32)
-
-    def step():
-        keys = oracle.quantize(pts, args.voxel)
-        om = oracle.OracleMap(3, sample_n, [4])
-        om.insert(keys, [vals])
-        om.find(keys)
-        act = om.active_indices()
-        _ = om.key_buffer()[act]
-        return 2 * sample_n
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    ops = 0
-    for _ in range(args.steps):
-        ops += step()
-    secs = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    pts = np.ascontiguousarray(workloads.voxel_scene_points(n=args.points, seed=0))
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        for _ in range(args.warmup):
+            oracle_all_cores_step(pts, args.voxel, pool, cores)
+        t0 = time.perf_counter()
+        ops = 0
+        for _ in range(args.steps):
+            ops += oracle_all_cores_step(pts, args.voxel, pool, cores)
+        secs = time.perf_counter() - t0
     value = ops / secs
-    sample = f"first {sample_n} of the {args.points} scene points per step, single-threaded C++ oracle"
+    sample = f"all {args.points} points per step, keys sharded over {cores} threads (one oracle map each)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "points": args.points, "voxel_m": args.voxel},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line, None)
     return 0
 
 
@@ -335,8 +331,75 @@ def cpu_baseline(args, pts_np):
         if el >= 10.0 or reps >= 40:
             break
     return {"value": ops / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} passes over the first {sample_n} points (quantize, insert, find, listing), "
-                      f"single-threaded C++ oracle, {el:.1f} s"}
+            "sample": f"first {sample_n} points x {reps} passes, 1 thread, {el:.0f} s"}
+
+
+def _owner(keys, parts):
+    """Shard of each int32x3 key: a multiply-xor spatial hash mod parts (the
+    partition of keys to host threads; any function of the key works)."""
+    k = keys.astype(np.uint32)
+    h = (k[:, 0] * np.uint32(73856093)) ^ (k[:, 1] * np.uint32(19349663)) ^ (k[:, 2] * np.uint32(83492791))
+    return (h % np.uint32(parts)).astype(np.int64)
+
+
+def oracle_all_cores_step(pts, voxel, pool, parts):
+    """One pass of the voxelization step on `parts` host threads: each thread
+    quantises a contiguous slice of the points and hashes its keys to owners;
+    then each thread runs its own sequential oracle map over the keys it owns
+    (insert with the point index as value, find, listing, key gather).  The
+    oracle's C calls release the interpreter lock, so the maps run in
+    parallel.  Returns the hash ops done (insert + find keys)."""
+    import oracle
+    oracle.quantize(pts[:1], voxel)  # loads (and if needed builds) the library before the threads use it
+    n = len(pts)
+    bounds = np.linspace(0, n, parts + 1).astype(np.int64)
+
+    def front(t):
+        lo, hi = bounds[t], bounds[t + 1]
+        k = oracle.quantize(pts[lo:hi], voxel)
+        own = _owner(k, parts)
+        order = np.argsort(own, kind="stable")
+        cuts = np.searchsorted(own[order], np.arange(parts + 1))
+        ids = np.arange(lo, hi, dtype=np.int32)[order]
+        ks = k[order]
+        return [(ks[cuts[j]:cuts[j + 1]], ids[cuts[j]:cuts[j + 1]]) for j in range(parts)]
+
+    pieces = list(pool.map(front, range(parts)))
+
+    def back(j):
+        kj = np.concatenate([pieces[t][j][0] for t in range(parts)])
+        vj = np.concatenate([pieces[t][j][1] for t in range(parts)])
+        om = oracle.OracleMap(3, max(1, len(kj)), [4])
+        om.insert(kj, [vj])
+        om.find(kj)
+        act = om.active_indices()
+        _ = om.key_buffer()[act]
+        return len(kj)
+
+    done = sum(pool.map(back, range(parts)))
+    assert done == n
+    return 2 * n
+
+
+def cpu_baseline_all_cores(args, pts_np, budget_s=10.0):
+    """The oracle sharded by key over every host core (one sequential map per
+    thread), on the same bounded sample as the single-threaded figure."""
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    sample_n = min(len(pts_np), 1_000_000)
+    pts = np.ascontiguousarray(pts_np[:sample_n])
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        oracle_all_cores_step(pts, args.voxel, pool, cores)  # warm-up (library load, pools)
+        ops, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            ops += oracle_all_cores_step(pts, args.voxel, pool, cores)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s or reps >= 100:
+                break
+    return {"value": ops / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample_n} points x {reps} passes, keys sharded over {cores} threads, {el:.0f} s"}
 
 
 def cpu_baseline_tsdf_frame(c):
@@ -361,6 +424,133 @@ def cpu_baseline_tsdf_frame(c):
     return {"ms_per_frame": 1000.0 * (t_int + t_rc), "cores": 1, "kind": "oracle",
             "sample": "frame 0 of the voxel-block pipeline: keys, double map and integration in full; ray casting "
                       "on every 97th pixel, scaled to the image"}
+
+
+# ------------------------------------------------------------ output line
+COMPACT_LIMIT = 1450  # bytes of the one stdout line
+
+
+def _sig(x, digits=4):
+    """Floats to `digits` significant digits (keeps the summary line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    return x
+
+
+def _pick(d, keys):
+    if not isinstance(d, dict):
+        return None
+    return {k: d[k] for k in keys if k in d}
+
+
+def highlights(full):
+    """A few figures of the side blocks for the summary line (G = 10^9):
+      graph_G:   the step replayed as a CUDA graph (G hash ops/s);
+      sweep:     the largest sweep point beyond 4x L2, activate and find as
+                 [G keys/s, fraction of the copy peak, fraction of the
+                 random-access roofline];
+      batched_G: [batched G ops/s, plain per-map G ops/s, batched p99 ms, plain p99 ms];
+      served:  per offered rate [req/s, p99 ms, sequential req/s, sequential p99 ms]."""
+    h = {}
+    g = full.get("graph_step")
+    if isinstance(g, dict) and "value" in g:
+        h["graph_G"] = g["value"] / 1e9
+    sw = full.get("sweep")
+    if isinstance(sw, dict):
+        big = [p_ for p_ in sw.get("points", []) if p_.get("working_set_x_l2", 0) >= 4]
+        if big:
+            p_ = max(big, key=lambda r: r["n"])
+            h["sweep"] = {"n": p_["n"], "rho": p_["rho"]}
+            for op, short in (("activate", "act"), ("find", "find")):
+                r = p_.get(op, {})
+                h["sweep"][short] = [(r.get("keys_per_s") or 0) / 1e9, r.get("frac_hbm"),
+                                     r.get("frac_random_access_roofline")]
+    b = full.get("batched")
+    if isinstance(b, dict) and "batched_graph" in b:
+        h["batched_G"] = [b["batched_graph"]["ops_per_s"] / 1e9, b["plain_per_map"]["ops_per_s"] / 1e9,
+                        b["batched_graph"]["ms_p99"], b["plain_per_map"]["ms_p99"]]
+    sv = full.get("serving")
+    if isinstance(sv, dict) and isinstance(sv.get("rates"), dict):
+        mode = sv.get("default_mode", "served")
+        rows = {"mode": mode}
+        for rate, e in sv["rates"].items():
+            s_, q_ = e.get(mode) or {}, e.get("sequential_plain") or {}
+            rows[rate] = [s_.get("req_per_s"), s_.get("p99_ms"), q_.get("req_per_s"), q_.get("p99_ms")]
+        h["served"] = rows
+    return h
+
+
+def compact_line(full, detail_path=None):
+    """The one stdout line: the contract's keys, the roofline, the CPU
+    baseline, the end-to-end figure, clocks and a few highlights.  Everything
+    else goes to the detail file."""
+    out = _pick(full, ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                       "scaling", "vs_baseline", "dtype", "data", "gpu_launches"))
+    if "impl" in full:
+        out = {"impl": full["impl"], **out}
+    out["config"] = _pick(full.get("config") or {}, ("workload", "points", "voxel_m", "unique_voxels", "l2",
+                                                     "parallelism", "sample"))
+    rl = full.get("roofline")
+    out["roofline"] = _pick(rl, ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic")) if rl else None
+    if isinstance(rl, dict) and rl.get("peak_kind"):
+        out["roofline"]["peak_kind"] = rl["peak_kind"].split(" ")[0]
+    cpu = full.get("cpu_baseline")
+    if isinstance(cpu, dict):
+        out["cpu_baseline"] = _pick(cpu, ("value", "unit", "cores", "kind", "sample"))
+        if isinstance(cpu.get("all_cores"), dict):
+            out["cpu_baseline"]["all_cores"] = _pick(cpu["all_cores"], ("value", "cores"))
+    else:
+        out["cpu_baseline"] = None
+    e2e = full.get("e2e")
+    out["e2e"] = _pick(e2e, ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "error")) \
+        if isinstance(e2e, dict) else None
+    clk = full.get("clocks")
+    out["clocks"] = _pick(clk, ("sm_mhz", "sm_max_mhz", "reasons", "samples_in_timed_region")) \
+        if isinstance(clk, dict) else None
+    hl = highlights(full)
+    if hl:
+        out["highlights"] = hl
+    if detail_path:
+        out["detail"] = os.path.basename(detail_path)
+    out = _sig(out)
+    line = json.dumps(out, separators=(",", ":"))
+    for drop in ("served_rows", "batched_G", "all"):
+        if len(line) <= COMPACT_LIMIT or "highlights" not in out:
+            break
+        h = out["highlights"]
+        if drop == "served_rows" and "served" in h:
+            rates = [k for k in h["served"] if k != "mode"]
+            h["served"] = {k: h["served"][k] for k in ["mode"] + rates[:1] + rates[-1:]}
+        elif drop == "all":
+            out.pop("highlights")
+        else:
+            h.pop(drop, None)
+        line = json.dumps(out, separators=(",", ":"))
+    if len(line) > COMPACT_LIMIT:
+        for k in ("config", "cpu_baseline"):
+            if isinstance(out.get(k), dict):
+                for kk in ("workload", "sample"):
+                    if isinstance(out[k].get(kk), str):
+                        out[k][kk] = out[k][kk][:120]
+        line = json.dumps(out, separators=(",", ":"))
+    return line
+
+
+def emit(full, detail_path):
+    """Writes the full results to detail_path (if given) and prints the
+    compact summary line last on stdout."""
+    if detail_path:
+        try:
+            with open(detail_path, "w") as fh:
+                json.dump(full, fh, indent=1)
+        except OSError as e:
+            print(f"bench: could not write {detail_path}: {e}", file=sys.stderr)
+            detail_path = None
+    print(compact_line(full, detail_path), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -786,18 +976,22 @@ def main(argv=None):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.lean:
         cpu = cpu_baseline(args, pts_np)
+        try:
+            cpu["all_cores"] = cpu_baseline_all_cores(args, pts_np)
+        except Exception as e:  # noqa: BLE001
+            cpu["all_cores"] = {"error": str(e)[:200]}
         if tsdf_cpu_inputs is not None:
             cpu["tsdf_frame"] = cpu_baseline_tsdf_frame(tsdf_cpu_inputs)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        full = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "points": N, "voxel_m": args.voxel, "key_dim": 3,
                            "unique_voxels": n_unique, "value": "int32 point index",
                            "step": "quantize || create, insert, find || (list active, gather unique keys), destroy "
                                    "(two streams, no host synchronisation inside a step)",
-                           "l2": "flushed between steps (256 MiB write outside the timed events)",
+                           "l2": "flushed (256 MiB write) between steps",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "graph_step": graph_step, "fused_quantize_step": fused,
@@ -806,7 +1000,7 @@ def main(argv=None):
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "ops": ops, "batched": batched, "serving": serving, "sweep": sweep, "tsdf_block_map": blocks, "tsdf": tsdf,
                 "source_digest": source_digest()}
-        print(json.dumps(line), flush=True)
+        emit(full, args.detail)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
