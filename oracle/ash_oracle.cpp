@@ -488,10 +488,9 @@ void om_tsdf_integrate(void* h, const int32_t* block_idx, int64_t n_blocks, int 
 // R^T [(px - cx) / fx, (py - cy) / fy, 1], so its parameter is the depth along
 // the optical axis.  Samples sit at depth t_i = depth_min + i * step,
 // i = 0..n_steps-1; sample i at p reads the nearest lattice point
-// g = floor(p * (1 / s) + 1/2) (the reciprocal taken once in float32), in
-// block K = floor(g / ell) at voxel v = g - K * ell,
-// and is valid when K is in the map
-// and the voxel's weight is positive.  The first pair of consecutive valid
+// g = floor(p / s + 1/2) (float32 division), in block K = floor(g / ell) at
+// voxel v = g - K * ell, and is valid when K is in the map and the voxel's
+// weight is positive.  The first pair of consecutive valid
 // samples with d_{i-1} > 0 >= d_i is the surface; its depth is
 // t_{i-1} + step * d_{i-1} / (d_{i-1} - d_i).  0 where no crossing is found.
 // value_bytes (4 or 8) is the element size of value buffers 0 (d) and 1 (w).
@@ -501,7 +500,6 @@ void om_tsdf_raycast(void* h, int ell, int value_bytes, const float* intr, const
   OracleMap* m = static_cast<OracleMap*>(h);
   const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
   const int64_t row = static_cast<int64_t>(ell) * ell * ell;
-  const float inv_voxel = div32(1.0f, voxel);
   auto value = [&](int buf, int64_t at) -> double {
     if (value_bytes == 8) return reinterpret_cast<const double*>(m->val_buf[buf].data())[at];
     return static_cast<double>(reinterpret_cast<const float*>(m->val_buf[buf].data())[at]);
@@ -528,7 +526,7 @@ void om_tsdf_raycast(void* h, int ell, int value_bytes, const float* intr, const
       int32_t g[3];
       bool in_range = true;
       for (int a = 0; a < 3; ++a) {
-        const float gf = std::floor(add32(mul32(add32(c[a], mul32(t, dw[a])), inv_voxel), 0.5f));
+        const float gf = std::floor(add32(div32(add32(c[a], mul32(t, dw[a])), voxel), 0.5f));
         if (!(gf > -1.0e9f && gf < 1.0e9f)) in_range = false;
         g[a] = in_range ? static_cast<int32_t>(gf) : 0;
       }

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) block_range_kernel(const int32_t* __
 // Thread per pixel.  The ray of pixel (px, py) leaves the camera centre along
 // R^T [(px - cx) / fx, (py - cy) / fy, 1]; sample i sits at depth
 // t_i = depth_min + i * step, at p = c + t_i * dir, and reads the nearest
-// lattice point g = floor(p * (1 / s) + 1/2) in block K = floor(g / ELL),
+// lattice point g = floor(p / s + 1/2) (IEEE float32 division) in block K = floor(g / ELL),
 // voxel v = g - K * ELL.  A sample is valid when K is in the map and its
 // weight is positive.  The first valid pair d_{i-1} > 0 >= d_i gives the depth
 // t_{i-1} + step * d_{i-1} / (d_{i-1} - d_i); 0 when there is none.  With a
@@ -358,13 +358,13 @@ struct RaySample {
 // i < 2^24, so the conversion to float32 is exact (and int32 keeps it off the
 // 64-bit conversion path).
 __device__ __forceinline__ RaySample ray_sample(const float (&c)[3], const float (&dw)[3], float depth_min,
-                                                float step, float inv_voxel, int32_t i) {
+                                                float step, float voxel, int32_t i) {
   RaySample r;
   r.in_range = true;
   const float t = __fadd_rn(depth_min, __fmul_rn(__int2float_rn(i), step));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float gf = floorf(__fadd_rn(__fmul_rn(__fadd_rn(c[a], __fmul_rn(t, dw[a])), inv_voxel), 0.5f));
+    const float gf = floorf(__fadd_rn(__fdiv_rn(__fadd_rn(c[a], __fmul_rn(t, dw[a])), voxel), 0.5f));
     r.in_range &= (gf > -1.0e9f && gf < 1.0e9f);
     r.g[a] = r.in_range ? static_cast<int32_t>(gf) : 0;
   }
@@ -376,7 +376,7 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
                                           const int32_t* __restrict__ local_values, int use_local,
                                           const float* __restrict__ tsdf, const float* __restrict__ weight,
                                           int32_t volume_capacity, const Cam& cam, int32_t width, int64_t pid,
-                                          float voxel, float inv_voxel, float depth_min, float step, float inv_step,
+                                          float voxel, float depth_min, float step, float inv_step,
                                           int32_t i_begin, int32_t n_steps) {
   constexpr int kVox = ELL * ELL * ELL;
   constexpr int kShift = ELL == 8 ? 3 : 4;
@@ -401,7 +401,7 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
   float out = 0.0f;
   for (int32_t i = i_begin; i < n_steps; ++i) {
     const float t = __fadd_rn(depth_min, __fmul_rn(__int2float_rn(i), step));
-    const RaySample r = ray_sample(c, dw, depth_min, step, inv_voxel, i);
+    const RaySample r = ray_sample(c, dw, depth_min, step, voxel, i);
     bool valid = false;
     float dcur = 0.0f;
     if (r.in_range) {
@@ -444,7 +444,7 @@ __device__ __forceinline__ float cast_ray(const TableView& tv, const TableView& 
           // confirm with the exact sample arithmetic; one step back if the
           // estimate crossed the face
           for (int tries = 0; tries < 2 && m > i; ++tries, --m) {
-            const RaySample rm = ray_sample(c, dw, depth_min, step, inv_voxel, m);
+            const RaySample rm = ray_sample(c, dw, depth_min, step, voxel, m);
             if (rm.in_range && (rm.g[0] >> kShift) == K[0] && (rm.g[1] >> kShift) == K[1] &&
                 (rm.g[2] >> kShift) == K[2]) {
               i = m;  // samples i+1..m are in the missing block
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) raycast_kernel(TableView tv, TableVi
                                                            const float* __restrict__ tsdf,
                                                            const float* __restrict__ weight, int32_t volume_capacity,
                                                            Cam cam, int32_t width, int64_t n_pixels, float voxel,
-                                                           float inv_voxel, float depth_min, float step,
+                                                           float depth_min, float step,
                                                            float inv_step, int32_t n_steps,
                                                            const unsigned int* __restrict__ zmin,
                                                            const unsigned int* __restrict__ zmax, int tiles_x,
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) raycast_kernel(TableView tv, TableVi
       {
         if (i0 < i1)
           out = cast_ray<ELL, S>(tv, local_tv, local_values, use_local, tsdf, weight, volume_capacity, cam, width, pid,
-                                 voxel, inv_voxel, depth_min, step, inv_step, i0, i1);
+                                 voxel, depth_min, step, inv_step, i0, i1);
       }
       depth_out[pid] = out;
     }
@@ -747,7 +747,6 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
   const float* weight = static_cast<const float*>(blocks->vb[weight_buffer]);
   const int32_t cap = static_cast<int32_t>(blocks->capacity);
   const int use_local = local_index_map ? 1 : 0;
-  const float inv_voxel = 1.0f / voxel_size;  // one IEEE division, the same on every host
   const float inv_step = 1.0f / step;
   // scratch: chunk counter | live count | tile zmin | tile zmax | live indices
   ash_map* lookup = local_index_map ? local_index_map : blocks;
@@ -794,8 +793,8 @@ ash_status ash_tsdf_raycast(ash_map* blocks, int tsdf_buffer, int weight_buffer,
   ash::TraceScope ts(ash::kKRaycast, st);
 #define ASH_RAYCAST(E, SB)                                                                                          \
   ash::vol::raycast_kernel<E, SB><<<grid, ash::vol::kThreads, 0, st>>>(tv, ltv, lvals, use_local, tsdf, weight, cap, \
-                                                                       cam, width, n_pix, voxel_size, inv_voxel,     \
-                                                                       depth_min, step, inv_step,                    \
+                                                                       cam, width, n_pix, voxel_size, depth_min,     \
+                                                                       step, inv_step,                               \
                                                                        static_cast<int32_t>(n_steps), zmin, zmax,   \
                                                                        tiles_x, use_range, counter, depth_out)
   if (ell == 8) {
