@@ -55,10 +55,14 @@ def parse_args(argv=None):
     p.add_argument("--batched-maps", type=int, default=64)
     p.add_argument("--no-serving", action="store_true", help="skip the serving latency figures")
     p.add_argument("--serving-rates", type=str, default="2000,5000,10000,20000,50000")
-    p.add_argument("--serving-requests", type=int, default=1000)
+    p.add_argument("--serving-requests", type=int, default=10000)
+    p.add_argument("--serving-repeats", type=int, default=3)
     p.add_argument("--no-tsdf", action="store_true", help="skip the voxel-block (TSDF) pipeline figures")
     p.add_argument("--no-blocks", action="store_true", help="skip the TSDF-shaped block-map figures")
     p.add_argument("--no-sweep", action="store_true", help="skip the uniqueness sweep")
+    p.add_argument("--no-voxel-sizes", action="store_true", help="skip the 5/10/20/50 mm voxel-size sweep")
+    p.add_argument("--sweep-only", action="store_true",
+                   help="run only the uniqueness sweep (for profiling one of its points) and print its result")
     p.add_argument("--sweep-points", type=str, default="",
                    help="override the sweep points, e.g. 20000000:0.5,1000000:1.0")
     p.add_argument("--block-frames", type=int, default=200)
@@ -230,6 +234,37 @@ def bytes_gather_keys(n, d=3):
 def bytes_erase(n_present, n_absent, d=3):
     """find + the slot rewrite (32) + the heap write (4) for each erased key."""
     return bytes_find(n_present, n_absent, d) + n_present * 36
+
+
+def split_find(n_hit, n_miss, d=3):
+    """bytes_find split into (random, streamed): the bucket sector and, on a
+    hit, the kB verify sector are random; the key row in and the index and
+    mask out are streamed."""
+    n = n_hit + n_miss
+    return 32 * n + 32 * n_hit, (4 * d + 5) * n
+
+
+def split_activate(n, n_win, d=3, heap_identity=True):
+    """bytes_claim + bytes_commit (no values) split into (random, streamed):
+    the claim's slot sector read and written back (64) and the commit's slot
+    rewrite (32 per winner) are random; key rows, slot indices, outputs,
+    winner bits, kB rows (written at consecutive indices i = t + rank) and
+    heap reads are streamed."""
+    total = bytes_claim(n, d) + bytes_commit(n, n_win, 0, d, heap_identity)
+    random = 64 * n + 32 * n_win
+    return random, total - random
+
+
+def random_access_fraction(ms, random_bytes, streamed_bytes, random_gbs, copy_gbs):
+    """Fraction of the random-access roofline: the time the probe needs for
+    the random sectors at the same footprint plus the time a copy needs for
+    the streamed bytes, over the measured time.  1.0 means the kernel moves
+    its random sectors as fast as the probe and its streamed bytes at copy
+    speed."""
+    if not random_gbs or not copy_gbs or ms <= 0:
+        return None
+    bound_s = random_bytes / (random_gbs * 1e9) + streamed_bytes / (copy_gbs * 1e9)
+    return bound_s / (ms / 1000.0)
 
 
 # The sources the insert claim / insert commit / find kernels compile from.
@@ -574,6 +609,12 @@ def main(argv=None):
         build.build()
     barrier(world)
     ash.lib()
+    if args.sweep_only:
+        hbm_peak, _ = peaks()
+        res = sweep_figures(args, device, hbm_peak)
+        if rank == 0:
+            print(json.dumps(_sig(res)), flush=True)
+        return 0
 
     N = args.points
     pts_np = workloads.voxel_scene_points(n=N, seed=rank)
@@ -585,7 +626,7 @@ def main(argv=None):
 
     aux = torch.cuda.Stream(device=device)
 
-    def step(points, keys_out):
+    def step(points, keys_out, voxel=args.voxel):
         # No host synchronisation anywhere in the step: the live count stays on
         # the device and bounds the gather of the unique voxel keys.  Two
         # streams overlap independent work: the map is created (table fill,
@@ -595,7 +636,7 @@ def main(argv=None):
         aux.wait_stream(main)
         with torch.cuda.stream(aux):
             hm = ash.HashMap(3, N, [(1,)], [torch.int32], device=device)
-        ash.ash_quantize(points, args.voxel, out=keys_out)
+        ash.ash_quantize(points, voxel, out=keys_out)
         main.wait_stream(aux)
         idx, mask = hm.insert(keys_out, [point_ids])
         aux.wait_stream(main)
@@ -758,9 +799,14 @@ def main(argv=None):
         for label, nbytes in (("table", table_bytes), ("512MiB", 512 << 20), ("8GiB", 8 << 30)):
             buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
             n_reads = 1 << 26
-            ms = timed_probe(lambda: ash.ash_probe_random_read(buf, n_reads, 32, sink, seed=7))
-            probe[f"read32_{label}_Gops"] = n_reads / (ms / 1000) / 1e9
-            probe[f"read32_{label}_GBps"] = n_reads * 32 / (ms / 1000) / 1e9
+            best = None
+            for loads in (4, 8, 16):
+                ms = timed_probe(lambda: ash.ash_probe_random_read(buf, n_reads, 32, sink, seed=7,
+                                                                   loads_per_thread=loads))
+                probe[f"read32_{label}_loads{loads}_Gops"] = n_reads / (ms / 1000) / 1e9
+                best = ms if best is None else min(best, ms)
+            probe[f"read32_{label}_Gops"] = n_reads / (best / 1000) / 1e9
+            probe[f"read32_{label}_GBps"] = n_reads * 32 / (best / 1000) / 1e9
             del buf
         tbl = torch.empty(table_bytes, dtype=torch.uint8, device=device)
         n_ops = N
@@ -938,6 +984,14 @@ def main(argv=None):
     except Exception as e:  # noqa: BLE001
         fused = {"error": str(e)[:200]}
 
+    # ---------------------------- the paper's voxel sizes (Sec. 6.1): 5-50 mm
+    voxel_sizes = None
+    if not args.lean and not args.no_voxel_sizes:
+        try:
+            voxel_sizes = voxel_size_figures(step, pts, keys, flush, N, hbm_peak, stream)
+        except Exception as e:  # noqa: BLE001
+            voxel_sizes = {"error": str(e)[:300]}
+
     # ------------------------------------------------- per-op figures (10^7)
     ops = None
     if not args.no_ops and not args.lean:
@@ -954,8 +1008,7 @@ def main(argv=None):
     sweep = None
     if not args.no_sweep and not args.lean:
         try:
-            rr = probe.get("read32_8GiB_GBps") if isinstance(probe, dict) else None
-            sweep = sweep_figures(args, device, hbm_peak, rr)
+            sweep = sweep_figures(args, device, hbm_peak)
         except Exception as e:  # noqa: BLE001
             sweep = {"error": str(e)[:300]}
 
@@ -998,13 +1051,59 @@ def main(argv=None):
                 "clocks": clocks.summary(), "kernels": kernels, "hash_op_roofline": op_roofline,
                 "random_access_roofline": probe,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "ops": ops, "batched": batched, "serving": serving, "sweep": sweep, "tsdf_block_map": blocks, "tsdf": tsdf,
+                "voxel_sizes": voxel_sizes, "ops": ops, "batched": batched, "serving": serving, "sweep": sweep, "tsdf_block_map": blocks, "tsdf": tsdf,
                 "source_digest": source_digest()}
         emit(full, args.detail)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def voxel_size_figures(step, pts, keys, flush, N, hbm_peak, stream, sizes=(0.005, 0.01, 0.02, 0.05), reps=30):
+    """The voxelization step at the paper's voxel sizes (Sec. 6.1: 5, 10, 20
+    and 50 mm) on the same 4M points: larger voxels mean more points per
+    voxel, so more of the insert's keys are duplicates that join an earlier
+    claim and lose.  Per size: unique voxels, median step time, hash ops/s,
+    and insert (claim + commit) and find as fractions of the copy peak by
+    algorithmic bytes, from per-kernel events."""
+    import torch
+    from paper_2110_00511_gb300 import ash
+    out = {"points": N, "sizes": []}
+    for vs in sizes:
+        for _ in range(3):
+            step(pts, keys, voxel=vs)
+        torch.cuda.synchronize()
+        ash.ash_trace_reset()
+        ev = []
+        for r in range(reps):
+            ash.ash_trace_enable(r % TRACE_EVERY == 0)  # per-kernel events on every 4th step only
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, count = step(pts, keys, voxel=vs)
+            e1.record(stream)
+            ev.append((e0, e1))
+        ash.ash_trace_enable(False)
+        torch.cuda.synchronize()
+        tr = ash.ash_trace_collect()
+        n_unique = int(count.item())
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        k_ms = {k: t / n for k, (t, n) in tr.items() if n}
+        rec = {"voxel_m": vs, "unique_voxels": n_unique, "points_per_voxel": N / max(1, n_unique),
+               "step_ms": ms, "hash_ops_per_s": 2 * N / (ms / 1000.0),
+               "kernel_ms": {k: k_ms[k] for k in ("quantize", "insert_claim", "insert_commit", "find") if k in k_ms}}
+        if "insert_claim" in k_ms and "insert_commit" in k_ms:
+            b_ins = bytes_claim(N) + bytes_commit(N, n_unique, 4)
+            t_ins = (k_ms["insert_claim"] + k_ms["insert_commit"]) / 1000.0
+            rec["insert"] = {"keys_per_s": N / t_ins, "algo_gbs": b_ins / t_ins / 1e9,
+                             "frac_hbm": b_ins / t_ins / 1e9 / hbm_peak}
+        if "find" in k_ms:
+            b_f = bytes_find(N, 0)
+            t_f = k_ms["find"] / 1000.0
+            rec["find"] = {"keys_per_s": N / t_f, "algo_gbs": b_f / t_f / 1e9, "frac_hbm": b_f / t_f / 1e9 / hbm_peak}
+        out["sizes"].append(rec)
+    return out
 
 
 def device_uniform_keys(n, rho, seed, device):
@@ -1025,13 +1124,40 @@ def device_uniform_keys(n, rho, seed, device):
     return distinct[pick].contiguous()
 
 
-def sweep_figures(args, device, hbm_peak, random_read_gbs):
+def probe_random_gbs(buf_bytes, device, reps=3):
+    """Random 32-byte sector reads over a buffer of buf_bytes, best over 8 and
+    16 loads in flight per thread and `reps` runs: (GB/s, G sectors/s)."""
+    import torch
+    from paper_2110_00511_gb300 import ash
+    buf = torch.empty(max(64, (buf_bytes + 63) // 64 * 64), dtype=torch.uint8, device=device)
+    sink = torch.zeros(4096, dtype=torch.int32, device=device)
+    n_reads = 1 << 26
+    best = None
+    for loads in (8, 16):
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ash.ash_probe_random_read(buf, n_reads, 32, sink, seed=17, loads_per_thread=loads)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    del buf
+    return n_reads * 32 / (best / 1000.0) / 1e9, n_reads / (best / 1000.0) / 1e9
+
+
+def sweep_figures(args, device, hbm_peak):
     """The uniqueness sweep of the voxelization setting (Sec. 5.1 / 6.1
-    shape): n uniform int32x3 keys at uniqueness rho, capacity n, activate
-    then find of the same keys, L2 flushed before each timed call.  Each
-    point reports ops/s, algorithmic GB/s, the fraction of the HBM copy peak
-    and of the random-access roofline (the 8 GiB random 32-byte read probe),
-    and its working set in multiples of L2."""
+    shape): n uniform int32x3 keys at uniqueness rho, capacity n, activate of
+    the keys, then find of the same keys in a fresh random order (so the kB
+    verify of a hit is a random access, as the byte model counts it), L2
+    flushed before each timed call.  Each point reports ops/s, algorithmic
+    GB/s, the fraction of the HBM copy peak, and the fraction of the
+    random-access roofline: the random-sector read probe run over a buffer of
+    the point's own random-access footprint (the buckets and kB rows of its
+    distinct keys; a point whose footprint fits in L2 gets none) gives the
+    rate for the random sectors, the copy peak the rate for the streamed bytes (see
+    random_access_fraction)."""
     import torch
     from paper_2110_00511_gb300 import ash
     l2 = torch.cuda.get_device_properties(device).L2_cache_size
@@ -1041,7 +1167,8 @@ def sweep_figures(args, device, hbm_peak, random_read_gbs):
     else:
         points = [(n, r) for n in (10_000, 100_000, 1_000_000, 10_000_000) for r in (0.1, 0.5, 1.0)]
         points += [(20_000_000, 0.5), (100_000_000, 0.5)]
-    out = {"l2_bytes": l2, "random_access_roofline_gbs": random_read_gbs, "points": []}
+    out = {"l2_bytes": l2, "copy_peak_gbs": hbm_peak, "points": [],
+           "find_queries": "the activated keys in a fresh random order"}
 
     def timed(fn, reps=3, make=None):
         best = None
@@ -1058,8 +1185,14 @@ def sweep_figures(args, device, hbm_peak, random_read_gbs):
             best = ms if best is None else min(best, ms)
         return best
 
+    clocks = ClockSampler(device.index)
+    clocks.__enter__()
+    t_start = time.time()
     for n, rho in points:
         keys = device_uniform_keys(n, rho, seed=1000 + n % 997 + int(rho * 10), device=device)
+        g = torch.Generator(device=device)
+        g.manual_seed(77 + n % 1000)
+        queries = keys[torch.randperm(n, generator=g, device=device)].contiguous()
         holder = {}
 
         def make():
@@ -1071,21 +1204,37 @@ def sweep_figures(args, device, hbm_peak, random_read_gbs):
             ms_act = timed(lambda hm: hm.activate(keys), make=make)
             hm = holder["hm"]
             n_unique = hm.size()
-            ms_find = timed(lambda _: hm.find(keys))
+            ms_find = timed(lambda _: hm.find(queries))
         t = hm.tuning()
-        slots = n * t.slots_per_capacity
-        working = int(slots * 8 + n * 16 + n * 12 + n * 5)   # table, kB, keys in, outputs
-        b_act = bytes_claim(n) + bytes_commit(n, n_unique, 0)
-        b_find = bytes_find(n, 0)
-        rec = {"n": n, "rho": rho, "unique": n_unique, "working_set_x_l2": working / l2}
-        for name, ms, nbytes in (("activate", ms_act, b_act), ("find", ms_find, b_find)):
-            gbs = nbytes / (ms / 1000.0) / 1e9
+        slots = int(n * t.slots_per_capacity)
+        # the random accesses touch one 32 B bucket per distinct key and its
+        # 16 B kB row: a map of few distinct keys stays in L2 however large
+        # its table is
+        footprint = min(slots * 8, n_unique * 32) + min(n * 16, n_unique * 16)
+        working = int(footprint + n * 12 + n * 5)   # + keys in, outputs
+        rec = {"n": n, "rho": rho, "unique": n_unique, "working_set_x_l2": working / l2,
+               "random_footprint_bytes": footprint}
+        r_gbs = None
+        if footprint >= l2:
+            with torch.cuda.nvtx.range(f"probe_{n}_{rho}"):
+                r_gbs, r_gsec = probe_random_gbs(footprint, device)
+            rec["probe_random_read_gbs"] = r_gbs
+            rec["probe_random_Gsectors"] = r_gsec
+        splits = {"activate": split_activate(n, n_unique), "find": split_find(n, 0)}
+        for name, ms in (("activate", ms_act), ("find", ms_find)):
+            rnd, stm = splits[name]
+            gbs = (rnd + stm) / (ms / 1000.0) / 1e9
             rec[name] = {"ms": ms, "keys_per_s": n / (ms / 1000.0), "algo_gbs": gbs, "frac_hbm": gbs / hbm_peak,
-                         "frac_random_access_roofline": gbs / random_read_gbs if random_read_gbs else None}
+                         "random_bytes": rnd, "streamed_bytes": stm,
+                         "random_Gsectors": rnd / 32 / (ms / 1000.0) / 1e9,
+                         "frac_random_access_roofline": random_access_fraction(ms, rnd, stm, r_gbs, hbm_peak)}
         out["points"].append(rec)
-        del hm, keys
+        del hm, keys, queries
         holder.clear()
         torch.cuda.empty_cache()
+    clocks.mark(t_start, time.time())
+    clocks.__exit__(None, None, None)
+    out["clocks"] = clocks.summary()
     return out
 
 
@@ -1439,26 +1588,38 @@ def _pct(xs, q):
 def serving_figures(args, device, n_tenants=16, clients=8):
     """Poisson arrivals over 16 resident tenant maps (int32x3 keys, one f32
     value), request sizes log-uniform in 1e3..1e6 keys, ops 30/60/10
-    insert/find/erase; request keys and values in pinned host memory.  Served
-    form: the native continuous-batching server, `clients` threads submitting
-    at their scheduled arrival times (staged with a copy at submit; staged
-    with DMA straight from the pinned request arrays; and, where the device
-    reads pageable host memory, zero-copy).  Baseline:
-    the same requests as sequential plain calls (upload, op, download) in
-    arrival order.  Latency = outputs on the host - scheduled arrival."""
-    import threading
+    insert/find/erase; request keys and values in pinned host memory.  Every
+    form replays the same traces from native threads (ash_server_replay /
+    ash_replay_sequential), so the client side adds no interpreter time:
+      served             the continuous-batching server, mode 0 (keys copied
+                         into pinned staging at submit);
+      served_pinned_dma  mode 2 (pinned request arrays uploaded by DMA, no
+                         CPU copy): the recommended form for callers whose
+                         request buffers are pinned, which is the case here;
+      served_zero_copy   mode 1 (kernels use the callers' arrays in place),
+                         where the device reads pageable host memory;
+      sequential_plain   the same requests as plain calls in arrival order
+                         (upload, op, download, synchronise).
+    Latency = outputs in the caller's arrays - scheduled arrival.  Each rate
+    runs `repeats` traces of `requests` requests; per form the median over
+    repeats is reported with the spread (min, max) of p50, p99 and req/s.
+    p99.9 is reported only when at least 1000 requests lie beyond it."""
     import torch
     from paper_2110_00511_gb300 import ash
     rng = np.random.default_rng(5)
     pool_n = 8_000_000
-    # request data lives in pinned host memory, as a serving frontend would
-    # keep it (every form reads the same arrays)
-    key_pool = torch.from_numpy(rng.integers(-(1 << 18), 1 << 18, size=(pool_n, 3)).astype(np.int32)).pin_memory().numpy()
-    val_pool = torch.from_numpy(rng.random(pool_n, dtype=np.float32)).pin_memory().numpy()
+    key_pool = torch.from_numpy(rng.integers(-(1 << 18), 1 << 18, size=(pool_n, 3)).astype(np.int32)).pin_memory()
+    val_pool = torch.from_numpy(rng.random(pool_n, dtype=np.float32)).pin_memory()
+    keys_np, vals_np = key_pool.numpy(), val_pool.numpy()
     ops_of = np.array([ash.ASH_OP_INSERT, ash.ASH_OP_FIND, ash.ASH_OP_ERASE])
     rates = [float(x) for x in args.serving_rates.split(",") if x]
-    R = args.serving_requests
-    out = {"tenants": n_tenants, "requests_per_rate": R, "client_threads": clients, "rates": {}}
+    R, reps = args.serving_requests, args.serving_repeats
+    out = {"tenants": n_tenants, "requests_per_trace": R, "repeats": reps, "client_threads": clients,
+           "default_mode": "served_pinned_dma",
+           "default_mode_reason": "request buffers are pinned: mode 2 uploads them by DMA with no CPU copy; the "
+                                  "server's API default stays mode 0, the only mode whose callers may reuse their "
+                                  "arrays as soon as submit returns",
+           "client": "native replay threads (no interpreter in the measured path)", "rates": {}}
 
     def make_trace(rate, seed):
         g = np.random.default_rng(seed)
@@ -1467,119 +1628,64 @@ def serving_figures(args, device, n_tenants=16, clients=8):
         ops = ops_of[g.choice(3, size=R, p=[0.3, 0.6, 0.1])]
         tenants = g.integers(0, n_tenants, size=R)
         starts = g.integers(0, pool_n - sizes)
-        return arr, sizes, ops, tenants, starts
+        return ash.Trace(arr, tenants, ops, sizes, starts, keys_np, vals_np)
 
     def summarize(lat_ms, keys_total, span_s):
-        return {"p50_ms": _pct(lat_ms, 0.50), "p99_ms": _pct(lat_ms, 0.99), "p999_ms": _pct(lat_ms, 0.999),
-                "req_per_s": len(lat_ms) / span_s, "keys_per_s": keys_total / span_s}
+        lat = np.sort(np.asarray(lat_ms))
+        rec = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "req_per_s": len(lat) / span_s, "keys_per_s": keys_total / span_s}
+        if len(lat) * 0.001 >= 1000:
+            rec["p999_ms"] = float(np.percentile(lat, 99.9))
+        return rec
 
-    srv = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
-                     device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256)
-    srv_dma = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
-                         device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
-                         zero_copy=2)
-    zc = ash.ash_get_device_info(device.index)["pageable_memory_access"] == 1
-    srv_zc = ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
-                        device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
-                        zero_copy=1) if zc else None
+    def mk(mode):
+        return ash.Server(n_tenants=n_tenants, key_dim=3, initial_capacity=1 << 20, value_row_bytes=4,
+                          device=device.index, staging_bytes=4 << 30, max_load=0.7, max_batch_requests=256,
+                          zero_copy=mode)
+
+    forms = {"served": mk(0), "served_pinned_dma": mk(2)}
+    if ash.ash_get_device_info(device.index)["pageable_memory_access"] == 1:
+        forms["served_zero_copy"] = mk(1)
     maps = [ash.HashMap(3, 1 << 20, [(1,)], [torch.float32], device=device) for _ in range(n_tenants)]
+    warm = make_trace(2000.0, 99)
+    warm.n_requests = min(warm.n_requests, 400)
+    for name, srv in forms.items():
+        srv.replay(warm, clients)
+    ash.replay_sequential(maps, warm)
 
-    def run_served(arr, sizes, ops, tenants, starts, srv=srv):
-        lat = [0.0] * len(arr)
-        rids = [None] * len(arr)
-        t0 = time.perf_counter() + 0.02
-
-        def client(c):
-            for r in range(c, len(arr), clients):
-                now = time.perf_counter()
-                if t0 + arr[r] > now:
-                    time.sleep(t0 + arr[r] - now)
-                lo, n = int(starts[r]), int(sizes[r])
-                vals = val_pool[lo:lo + n] if ops[r] == ash.ASH_OP_INSERT else None
-                rids[r] = (srv.submit(int(tenants[r]), int(ops[r]), key_pool[lo:lo + n], vals), time.perf_counter())
-
-        th = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
-        for t in th:
-            t.start()
-        done_at = [0.0] * len(arr)
-        for r in range(len(arr)):
-            while rids[r] is None:
-                time.sleep(0.0002)
-            rid, t_sub = rids[r]
-            _, _, server_ms = srv.wait(rid)
-            lat[r] = (t_sub - (t0 + arr[r])) * 1000.0 + server_ms   # client lag + submit-to-result
-            done_at[r] = t_sub + server_ms / 1000.0
-        for t in th:
-            t.join()
-        return lat, max(done_at) - t0
-
-    def run_sequential(arr, sizes, ops, tenants, starts):
-        lat = []
-        t0 = time.perf_counter() + 0.02
-        t_end = t0
-        for r in range(len(arr)):
-            now = time.perf_counter()
-            if t0 + arr[r] > now:
-                time.sleep(t0 + arr[r] - now)
-            lo, n = int(starts[r]), int(sizes[r])
-            k = torch.from_numpy(key_pool[lo:lo + n]).to(device)
-            hm = maps[int(tenants[r])]
-            if ops[r] == ash.ASH_OP_INSERT:
-                i, m = hm.insert(k, [torch.from_numpy(val_pool[lo:lo + n]).to(device)])
-            elif ops[r] == ash.ASH_OP_FIND:
-                i, m = hm.find(k)
-            else:
-                i, m = None, hm.erase(k)
-            m.cpu().numpy()
-            if i is not None:
-                i.cpu().numpy()
-            t_end = time.perf_counter()
-            lat.append((t_end - (t0 + arr[r])) * 1000.0)
-        return lat, t_end - t0
-
-    # warm both forms (pinned staging classes, device pools, first growth) untimed
-    warm = make_trace(1000.0, 99)
-    run_served(*warm)
-    run_served(*warm, srv=srv_dma)
-    if srv_zc is not None:
-        run_served(*warm, srv=srv_zc)
-    run_sequential(*warm)
     for ri, rate in enumerate(rates):
-        trace = make_trace(rate, 100 + ri)
-        keys_total = int(trace[1].sum())
-        st0 = srv.stats()
-        lat, span = run_served(*trace)
-        st1 = srv.stats()
-        served = summarize(lat, keys_total, span)
-        nb = st1["batches"] - st0["batches"]
-        served["avg_requests_per_batch"] = (st1["batched_requests"] - st0["batched_requests"]) / max(1, nb)
-        served["growth_rehashes"] = st1["rehashes"] - st0["rehashes"]
-        entry = {"served": served}
-        d0 = srv_dma.stats()
-        dlat, dspan = run_served(*trace, srv=srv_dma)
-        d1 = srv_dma.stats()
-        ds = summarize(dlat, keys_total, dspan)
-        db = d1["batches"] - d0["batches"]
-        ds["avg_requests_per_batch"] = (d1["batched_requests"] - d0["batched_requests"]) / max(1, db)
-        ds["growth_rehashes"] = d1["rehashes"] - d0["rehashes"]
-        entry["served_pinned_dma"] = ds
-        if srv_zc is not None:
-            z0 = srv_zc.stats()
-            zlat, zspan = run_served(*trace, srv=srv_zc)
-            z1 = srv_zc.stats()
-            zs = summarize(zlat, keys_total, zspan)
-            zb = z1["batches"] - z0["batches"]
-            zs["avg_requests_per_batch"] = (z1["batched_requests"] - z0["batched_requests"]) / max(1, zb)
-            zs["growth_rehashes"] = z1["rehashes"] - z0["rehashes"]
-            entry["served_zero_copy"] = zs
-        seq_lat, seq_span = run_sequential(*trace)
-        entry["sequential_plain"] = summarize(seq_lat, keys_total, seq_span)
-        entry["offered_keys_per_s"] = keys_total / float(trace[0][-1])
+        runs = {k: [] for k in list(forms) + ["sequential_plain"]}
+        batches = {k: [0, 0, 0] for k in forms}
+        offered = []
+        for rep in range(reps):
+            tr = make_trace(rate, 100 + 10 * ri + rep)
+            keys_total = int(tr.n.sum())
+            offered.append(keys_total / float(tr.arrival_s[-1]))
+            for name, srv in forms.items():
+                st0 = srv.stats()
+                lat, span = srv.replay(tr, clients)
+                st1 = srv.stats()
+                runs[name].append(summarize(lat, keys_total, span))
+                batches[name][0] += st1["batches"] - st0["batches"]
+                batches[name][1] += st1["batched_requests"] - st0["batched_requests"]
+                batches[name][2] += st1["rehashes"] - st0["rehashes"]
+            lat, span = ash.replay_sequential(maps, tr)
+            runs["sequential_plain"].append(summarize(lat, keys_total, span))
+        entry = {"offered_keys_per_s": float(np.median(offered))}
+        for name, recs in runs.items():
+            agg = {}
+            for k in recs[0]:
+                vals = [r_[k] for r_ in recs]
+                agg[k] = float(np.median(vals))
+                agg[k + "_range"] = [float(min(vals)), float(max(vals))]
+            if name in batches:
+                nb, nr, nrh = batches[name]
+                agg["avg_requests_per_batch"] = nr / max(1, nb)
+                agg["growth_rehashes"] = nrh
+            entry[name] = agg
         out["rates"][str(int(rate))] = entry
-    srv.close()
-    srv_dma.close()
-    if srv_zc is not None:
-        srv_zc.close()
+    for srv in forms.values():
+        srv.close()
     del maps
     return out
 

@@ -164,10 +164,6 @@ ash_status ash_activate(ash_map* map, const int32_t* keys, int64_t n, int32_t* b
 ash_status ash_find(ash_map* map, const int32_t* keys, int64_t n, int32_t* buf_indices,
                     uint8_t* masks, ash_stream stream);
 
-/* Erase: removes each stored key and returns its buffer index to the heap.
- *   masks: uint8 [n] out; 1 at the first position of each key that was
- *          stored, 0 elsewhere.
- * Uses n * 4 bytes of library-owned scratch (grown on demand). */
 /* The same operations on float32 points [n, key_dim]: each row's key is
  * floor(p / cell) per coordinate, computed where the row is read, with an
  * IEEE float32 division and rounding toward minus infinity (bit-identical to
@@ -181,6 +177,12 @@ ash_status ash_activate_points(ash_map* map, const float* points, float cell, in
 ash_status ash_find_points(ash_map* map, const float* points, float cell, int64_t n, int32_t* buf_indices,
                            uint8_t* masks, ash_stream stream);
 
+/* Erase: removes each stored key and returns its buffer index to the heap.
+ *   masks: uint8 [n] out; 1 at the first position of each key that was
+ *          stored, 0 elsewhere.
+ * Uses n * 4 bytes of map-owned scratch, grown on demand (a device
+ * allocation the first time a batch is larger than any before it; see
+ * ash_erase_noalloc for the form that allocates nothing). */
 ash_status ash_erase(ash_map* map, const int32_t* keys, int64_t n, uint8_t* masks, ash_stream stream);
 
 /* Allocation-free erase.  The paper has no counterpart: this entry point
@@ -399,6 +401,42 @@ ash_status ash_server_stats_get(ash_server* server, ash_server_stats* out_host);
 ash_status ash_server_map(ash_server* server, int32_t tenant, ash_map** out_host);
 ash_status ash_server_stream(ash_server* server, ash_stream* out_host);
 
+/* Serving replay (measurement support, not part of the map): a request trace
+ * replayed from native threads, so that the measured latencies are the
+ * server's and not a scripting-language client's.  Request r is op[r] on
+ * tenant[r] over the n[r] key rows starting at row[r] of keys_host
+ * ([rows, key_dim] int32, host memory; pinned arrays let zero_copy mode 2
+ * upload them by DMA) and, for inserts, the same rows of values_host
+ * ([rows] value rows).  arrival_s[r] is its arrival time in seconds after
+ * the start (non-decreasing).  Outputs go to host arrays the replay recycles
+ * by size class.
+ *   ash_server_replay: `threads` submitter threads submit request r (r mod
+ *     threads) at its arrival time, one tenant's requests in trace order
+ *     (a request waits for the submit of its tenant's previous one); as
+ *     many waiter threads wait for them.
+ *   ash_replay_sequential: the same trace as plain calls in arrival order on
+ *     maps[tenant] (one value buffer at most, shared layout): upload, the
+ *     operation, download, synchronise; the next request starts after.
+ * latency_ms_host[r]: from arrival to outputs in the caller's arrays (-1 for
+ * a request that failed).  *span_s_host: start to the last completion.
+ * Both return after every request finished; errors: ASH_ERR_INVALID for a
+ * bad trace (checked before anything runs), else the first failed call. */
+typedef struct ash_replay_trace {
+  int64_t n_requests;
+  const double* arrival_s;
+  const int32_t* tenant;
+  const int32_t* op;          /* ash_op */
+  const int64_t* n;
+  const int64_t* row;
+  int64_t rows;               /* rows of keys_host (and values_host) */
+  const int32_t* keys_host;
+  const void* values_host;
+} ash_replay_trace;
+ash_status ash_server_replay(ash_server* server, const ash_replay_trace* trace, int32_t threads,
+                             double* latency_ms_host, double* span_s_host);
+ash_status ash_replay_sequential(ash_map* const* maps, int32_t n_maps, const ash_replay_trace* trace,
+                                 double* latency_ms_host, double* span_s_host);
+
 /* Voxel quantisation (Sec. 6.1 listing; Eq. (10) with s*l as the cell edge):
  * keys[j] = floor(points[j] / cell) per coordinate, computed in float32 with
  * IEEE division and rounding toward minus infinity, for n_coords floats.
@@ -408,11 +446,14 @@ ash_status ash_quantize(const float* points, int64_t n_coords, float cell, int32
 
 /* Random-sector read probe (measurement only, not part of the map): n_reads
  * reads of sector_bytes (32 or 64) at pseudo-random sector-aligned offsets of
- * buf (buf_bytes, multiple of 64), XOR-folded into sink[0..grid).  Sets the
- * random-access roofline the map kernels are compared with. */
+ * buf (buf_bytes, multiple of 64, 64-byte aligned), XOR-folded into
+ * sink[0..sink_len).  Each thread of a grid of 8 blocks of 256 threads per SM
+ * keeps loads_per_thread (4, 8 or 16) independent reads in flight.  Run over
+ * a buffer of a kernel's random-access footprint, it sets the random-access
+ * roofline that kernel is compared with. */
 ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_reads,
-                                 int sector_bytes, uint32_t seed, uint32_t* sink, int64_t sink_len,
-                                 ash_stream stream);
+                                 int sector_bytes, int loads_per_thread, uint32_t seed, uint32_t* sink,
+                                 int64_t sink_len, ash_stream stream);
 
 /* Kernel tracing (measurement support, not part of the map).  The library
  * counts every kernel it launches; with tracing on it also records a CUDA
@@ -505,7 +546,7 @@ ash_status ash_tsdf_integrate(ash_map* blocks, int tsdf_buffer, int weight_buffe
  * dir = R^T [(px - cx) / fx, (py - cy) / fy, 1], so its parameter is the depth
  * along the optical axis.  Sample i (0 <= i < n_steps) sits at
  * t_i = depth_min + i * step, p = c + t_i * dir, and reads the nearest lattice
- * point g = floor(p * r + 1/2), r = 1 / voxel_size in float32: block K = floor(g / l), voxel
+ * point g = floor(p / voxel_size + 1/2) (IEEE float32 division): block K = floor(g / l), voxel
  * v = g - K * l.  It is valid when K is in the map and w > 0.  The first pair
  * of consecutive valid samples with d_{i-1} > 0 >= d_i gives the depth
  * t_{i-1} + step * d_{i-1} / (d_{i-1} - d_i); pixels without one get 0.

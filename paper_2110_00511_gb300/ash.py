@@ -76,6 +76,12 @@ class DeviceInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ReplayTrace(ctypes.Structure):
+    _fields_ = [("n_requests", ctypes.c_int64), ("arrival_s", ctypes.c_void_p), ("tenant", ctypes.c_void_p),
+                ("op", ctypes.c_void_p), ("n", ctypes.c_void_p), ("row", ctypes.c_void_p), ("rows", ctypes.c_int64),
+                ("keys_host", ctypes.c_void_p), ("values_host", ctypes.c_void_p)]
+
+
 class BatchOp(ctypes.Structure):
     _fields_ = [("map", ctypes.c_void_p), ("op", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_int64),
@@ -119,7 +125,7 @@ _SIGS = {
     "ash_set_tuning": (_I32, [_P, ctypes.POINTER(Tuning)]),
     "ash_sync_status": (_I32, [_P, _P]),
     "ash_quantize": (_I32, [_P, _I64, ctypes.c_float, _P, _P]),
-    "ash_probe_random_read": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
+    "ash_probe_random_read": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
     "ash_probe_random_atomic": (_I32, [_P, _I64, _I64, ctypes.c_int, ctypes.c_uint32, _P, _I64, _P]),
     "ash_trace_kernel_kinds": (ctypes.c_int, []),
     "ash_trace_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -140,6 +146,8 @@ _SIGS = {
     "ash_server_stats_get": (_I32, [_P, ctypes.POINTER(ServerStats)]),
     "ash_server_map": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
     "ash_server_stream": (_I32, [_P, ctypes.POINTER(_P)]),
+    "ash_server_replay": (_I32, [_P, ctypes.POINTER(ReplayTrace), _I32, _P, ctypes.POINTER(ctypes.c_double)]),
+    "ash_replay_sequential": (_I32, [_P, _I32, ctypes.POINTER(ReplayTrace), _P, ctypes.POINTER(ctypes.c_double)]),
     "ash_depth_to_block_keys": (_I32, [_P, _I32, _I32, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P,
                                        ctypes.POINTER(_I64), _P]),
     "ash_double_map_activate": (_I32, [_P, _P, _P, _I64, _P, _P, _P, ctypes.POINTER(_I64), _P]),
@@ -179,6 +187,17 @@ def _check(status):
 
 def _stream(device=None):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream_of(device_index):
+    """The current CUDA stream of a device as an integer handle (the fast
+    route of the map methods; same stream as _stream)."""
+    if _raw_stream is not None:
+        return _raw_stream(device_index)
+    return torch.cuda.current_stream(device_index).cuda_stream
 
 
 def _ptr(t):
@@ -294,7 +313,26 @@ def ash_erase_noalloc(handle, keys, masks, stream=None):
     cannot let a library allocate (fully budgeted device memory, or loops
     where a first-time allocation may synchronise the device).  Uses a fixed
     4 MiB device array shared by all calls; n <= ASH_ERASE_NOALLOC_MAX_KEYS;
-    calls that can overlap on the GPU must be ordered by the caller."""
+    calls that can overlap on the GPU must be ordered by the caller.
+
+    keys: contiguous int32 CUDA tensor [n, key_dim]; masks: contiguous bool or
+    uint8 CUDA tensor on the same device with at least n elements.  Anything
+    else raises ValueError before the library is called, so the kernels never
+    see a short or mistyped array."""
+    if not isinstance(keys, torch.Tensor) or not isinstance(masks, torch.Tensor):
+        raise ValueError("keys and masks must be torch tensors")
+    _need_cuda(keys, "keys", torch.int32)
+    if keys.dim() != 2:
+        raise ValueError("keys must be int32 [n, key_dim]")
+    if handle is not None and keys.shape[1] != lib().ash_key_dim(handle):
+        raise ValueError("keys must have the map's key_dim columns")
+    if masks.dtype not in (torch.bool, torch.uint8):
+        raise ValueError("masks must be bool or uint8")
+    _need_cuda(masks, "masks")
+    if masks.device != keys.device:
+        raise ValueError("keys and masks must be on the same device")
+    if masks.numel() < keys.shape[0]:
+        raise ValueError("masks must hold at least n elements")
     _check(lib().ash_erase_noalloc(handle, _ptr(keys), keys.shape[0], _ptr(masks),
                                    stream if stream is not None else _stream(keys.device)))
 
@@ -353,9 +391,9 @@ def ash_probe_random_atomic(buf, n_ops, mode, sink, seed=0, stream=None):
                                          stream if stream is not None else _stream(buf.device)))
 
 
-def ash_probe_random_read(buf, n_reads, sector_bytes, sink, seed=0, stream=None):
+def ash_probe_random_read(buf, n_reads, sector_bytes, sink, seed=0, loads_per_thread=8, stream=None):
     _check(lib().ash_probe_random_read(_ptr(buf), buf.numel() * buf.element_size(), int(n_reads), int(sector_bytes),
-                                       ctypes.c_uint32(seed), _ptr(sink), sink.numel(),
+                                       int(loads_per_thread), ctypes.c_uint32(seed), _ptr(sink), sink.numel(),
                                        stream if stream is not None else _stream(buf.device)))
 
 
@@ -498,10 +536,61 @@ class Server:
         _check(lib().ash_server_stats_get(self._h, ctypes.byref(st)))
         return st.as_dict()
 
+    def replay(self, trace, threads=8):
+        """Replays a request trace (see make_trace) from native threads:
+        (latency_ms per request, span seconds)."""
+        import numpy as np
+        tr, keep = trace.as_struct()
+        lat = np.empty(trace.n_requests, np.float64)
+        span = ctypes.c_double()
+        _check(lib().ash_server_replay(self._h, ctypes.byref(tr), int(threads), lat.ctypes.data, ctypes.byref(span)))
+        return lat, span.value
+
     def map_handle(self, tenant):
         h = ctypes.c_void_p()
         _check(lib().ash_server_map(self._h, int(tenant), ctypes.byref(h)))
         return h
+
+
+class Trace:
+    """A serving trace for the native replays: request r is op[r] on
+    tenant[r] over rows row[r]:row[r]+n[r] of keys (int32 [rows, key_dim],
+    host) and values (host, inserts), arriving arrival_s[r] seconds after
+    the start."""
+
+    def __init__(self, arrival_s, tenant, op, n, row, keys, values=None):
+        import numpy as np
+        self.arrival_s = np.ascontiguousarray(arrival_s, np.float64)
+        self.tenant = np.ascontiguousarray(tenant, np.int32)
+        self.op = np.ascontiguousarray(op, np.int32)
+        self.n = np.ascontiguousarray(n, np.int64)
+        self.row = np.ascontiguousarray(row, np.int64)
+        if not (len(self.arrival_s) == len(self.tenant) == len(self.op) == len(self.n) == len(self.row)):
+            raise ValueError("trace arrays differ in length")
+        if keys.ndim != 2 or keys.dtype != np.int32 or not keys.flags.c_contiguous:
+            raise ValueError("keys must be contiguous int32 [rows, key_dim]")
+        if values is not None and (values.shape[0] != keys.shape[0] or not values.flags.c_contiguous):
+            raise ValueError("values must be contiguous with one row per key row")
+        self.keys, self.values = keys, values
+        self.n_requests = len(self.arrival_s)
+
+    def as_struct(self):
+        t = ReplayTrace(self.n_requests, self.arrival_s.ctypes.data, self.tenant.ctypes.data, self.op.ctypes.data,
+                        self.n.ctypes.data, self.row.ctypes.data, self.keys.shape[0], self.keys.ctypes.data,
+                        self.values.ctypes.data if self.values is not None else None)
+        return t, self
+
+
+def replay_sequential(maps, trace):
+    """The trace as plain calls in arrival order on maps[tenant] (upload, op,
+    download, synchronise): (latency_ms per request, span seconds)."""
+    import numpy as np
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle.value for m in maps])
+    tr, keep = trace.as_struct()
+    lat = np.empty(trace.n_requests, np.float64)
+    span = ctypes.c_double()
+    _check(lib().ash_replay_sequential(arr, len(maps), ctypes.byref(tr), lat.ctypes.data, ctypes.byref(span)))
+    return lat, span.value
 
 
 # -------------------------------------------------------------------- class
@@ -544,9 +633,13 @@ class HashMap:
             self._h = None
 
     def _keys(self, keys):
-        _need_cuda(keys, "keys", torch.int32)
-        if keys.dim() != 2 or keys.shape[1] != self.key_dim:
-            raise ValueError(f"keys must be int32 [N, {self.key_dim}]")
+        # one combined test on the common path; the detailed checks name the problem
+        if (keys.dtype is not torch.int32 or keys.dim() != 2 or keys.shape[1] != self.key_dim
+                or keys.get_device() != self.device.index or not keys.is_contiguous()):
+            _need_cuda(keys, "keys", torch.int32)
+            if keys.dim() != 2 or keys.shape[1] != self.key_dim:
+                raise ValueError(f"keys must be int32 [N, {self.key_dim}]")
+            raise ValueError("keys must be on the map's device")
         return keys
 
     def _outputs(self, n):
@@ -562,27 +655,58 @@ class HashMap:
             _need_cuda(v, "values", dt)
             if v.numel() != keys.shape[0] * torch.Size(shp).numel():
                 raise ValueError("value tensor does not match [N, *shape]")
-        idx, mask = self._outputs(keys.shape[0])
-        ash_insert(self._h, keys, values, idx, mask)
+            if v.get_device() != self.device.index:
+                raise ValueError("values must be on the map's device")
+        n = keys.shape[0]
+        idx, mask = self._outputs(n)
+        arr = (ctypes.c_void_p * max(1, len(values)))(*[v.data_ptr() for v in values])
+        st = lib().ash_insert(self._h, keys.data_ptr(), arr, n, idx.data_ptr(), mask.data_ptr(),
+                              _stream_of(self.device.index))
+        if st:
+            _check(st)
         return idx, mask
 
     def activate(self, keys):
         keys = self._keys(keys)
-        idx, mask = self._outputs(keys.shape[0])
-        ash_activate(self._h, keys, idx, mask)
+        n = keys.shape[0]
+        idx, mask = self._outputs(n)
+        st = lib().ash_activate(self._h, keys.data_ptr(), n, idx.data_ptr(), mask.data_ptr(),
+                                _stream_of(self.device.index))
+        if st:
+            _check(st)
         return idx, mask
 
     def find(self, keys):
         keys = self._keys(keys)
-        idx, mask = self._outputs(keys.shape[0])
-        ash_find(self._h, keys, idx, mask)
+        n = keys.shape[0]
+        idx, mask = self._outputs(n)
+        st = lib().ash_find(self._h, keys.data_ptr(), n, idx.data_ptr(), mask.data_ptr(),
+                            _stream_of(self.device.index))
+        if st:
+            _check(st)
         return idx, mask
 
     def erase(self, keys):
         keys = self._keys(keys)
-        mask = torch.empty(keys.shape[0], dtype=torch.bool, device=self.device)
-        ash_erase(self._h, keys, mask)
+        n = keys.shape[0]
+        mask = torch.empty(n, dtype=torch.bool, device=self.device)
+        st = lib().ash_erase(self._h, keys.data_ptr(), n, mask.data_ptr(), _stream_of(self.device.index))
+        if st:
+            _check(st)
         return mask
+
+    def erase_noalloc(self, keys, masks=None):
+        """Erase through ash_erase_noalloc: the library allocates nothing (its
+        per-key scratch is a fixed device array); n <= ASH_ERASE_NOALLOC_MAX_KEYS.
+        `masks` (bool [n] on the map's device) may be given to avoid the output
+        allocation too."""
+        keys = self._keys(keys)
+        if keys.device != self.device:
+            raise ValueError("keys must be on the map's device")
+        if masks is None:
+            masks = torch.empty(keys.shape[0], dtype=torch.bool, device=self.device)
+        ash_erase_noalloc(self._h, keys, masks)
+        return masks
 
     def active_indices(self):
         out = torch.empty(max(1, self.capacity()), dtype=torch.int32, device=self.device)

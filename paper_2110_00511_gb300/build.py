@@ -28,7 +28,7 @@ def _nvcc():
 
 
 def _units():
-    units = [("ash_map.cu", []), ("ash_aux.cu", []), ("ash_trace.cu", []), ("ash_batch.cu", []), ("ash_tune.cu", []), ("ash_server.cu", []),
+    units = [("ash_map.cu", []), ("ash_aux.cu", []), ("ash_trace.cu", []), ("ash_batch.cu", []), ("ash_tune.cu", []), ("ash_server.cu", []), ("ash_replay.cu", []),
              ("ash_volume.cu", [])]
     units += [("ash_dim.cu", [f"-DASH_DIM={d}"]) for d in range(1, 9)]
     return units

@@ -320,13 +320,12 @@ void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, con
 // ----------------------------------------------------------- roofline probe
 // Each thread performs reads at pseudo-random sector-aligned offsets (a
 // splitmix64 sequence), XOR-folds them and writes one word per block, so the
-// loads cannot be removed.  Several independent reads are in flight per
-// thread.
-template <int SECTOR>
+// loads cannot be removed.  UNROLL independent reads are issued before any of
+// them is used, so each thread keeps UNROLL requests in flight.
+template <int SECTOR, int UNROLL>
 __global__ void __launch_bounds__(256) probe_kernel(const uint64_t* __restrict__ buf, uint64_t n_sectors,
                                                     int64_t n_reads, uint32_t seed, uint32_t* __restrict__ sink,
                                                     int64_t sink_len) {
-  constexpr int UNROLL = 4;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
   uint64_t acc = 0;
@@ -399,15 +398,23 @@ void launch_probe_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, 
                                                                   sink, sink_len);
 }
 
-void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
-                  int64_t sink_len, const Launch& L) {
+void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, int loads_per_thread,
+                  uint32_t seed, uint32_t* sink, int64_t sink_len, const Launch& L) {
   const uint64_t n_sectors = static_cast<uint64_t>(buf_bytes) / static_cast<uint64_t>(sector);
   const int grid = L.grid_cap;
+  const uint64_t* b = static_cast<const uint64_t*>(buf);
   TraceScope ts(kKProbe, L.stream);
-  if (sector == 64)
-    probe_kernel<64><<<grid, L.block, 0, L.stream>>>(static_cast<const uint64_t*>(buf), n_sectors, n_reads, seed, sink, sink_len);
-  else
-    probe_kernel<32><<<grid, L.block, 0, L.stream>>>(static_cast<const uint64_t*>(buf), n_sectors, n_reads, seed, sink, sink_len);
+#define ASH_PROBE(SEC, U) probe_kernel<SEC, U><<<grid, L.block, 0, L.stream>>>(b, n_sectors, n_reads, seed, sink, sink_len)
+  if (sector == 64) {
+    if (loads_per_thread == 16) ASH_PROBE(64, 16);
+    else if (loads_per_thread == 8) ASH_PROBE(64, 8);
+    else ASH_PROBE(64, 4);
+  } else {
+    if (loads_per_thread == 16) ASH_PROBE(32, 16);
+    else if (loads_per_thread == 8) ASH_PROBE(32, 8);
+    else ASH_PROBE(32, 4);
+  }
+#undef ASH_PROBE
 }
 
 }  // namespace ash

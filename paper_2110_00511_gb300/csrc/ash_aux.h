@@ -32,7 +32,7 @@ void launch_gather_values(const void* src, int64_t row_bytes, int vec, int64_t c
 void launch_quantize(const float* pts, int64_t n, float cell, int32_t* keys, const Launch& L);
 void launch_probe_atomic(void* buf, int64_t buf_bytes, int64_t n_ops, int mode, uint32_t seed, uint32_t* sink,
                          int64_t sink_len, const Launch& L);
-void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, uint32_t seed, uint32_t* sink,
-                  int64_t sink_len, const Launch& L);
+void launch_probe(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector, int loads_per_thread,
+                  uint32_t seed, uint32_t* sink, int64_t sink_len, const Launch& L);
 
 }  // namespace ash

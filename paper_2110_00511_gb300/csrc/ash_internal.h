@@ -45,6 +45,7 @@ struct ash_map {
   int64_t scratch_bytes = 0;
   uint32_t* win_bits = nullptr;    // insert: winner flags, one bit per key
   int64_t win_bits_bytes = 0;
+  bool win_bits_clean = true;      // every winner flag is clear (the commit clears what it read)
   void* list_scratch = nullptr;    // listing: free-index bitmap + block counts
   int64_t list_scratch_bytes = 0;
   int64_t size_ub = 0;  // upper bound of live entries since the last sync
@@ -118,6 +119,8 @@ void invalidate_snapshot(ash_map* m);
 void maybe_snapshot(ash_map* m, cudaStream_t st);
 // Records the stream of an insert/activate (snapshots need a single one).
 void note_insert_stream(ash_map* m, cudaStream_t st);
+// Key dimension, value row bytes and tenant count of a server.
+void server_layout(const ash_server* s, int* key_dim, int* value_row_bytes, int* n_tenants);
 
 }  // namespace host
 }  // namespace ash

@@ -730,7 +730,17 @@ __device__ __forceinline__ void commit_tile(const TableView& t, const In& keys, 
     }
   }
   int total;
-  const int off = block_exclusive_scan(cnt, total, s_warp);
+  const int off = block_exclusive_scan(cnt, total, s_warp);  // a block barrier: every flag word was read
+  if constexpr (FLAGS) {
+    // leave the flags clear for the next insert (one lane per 32 positions;
+    // blockDim and the tile base are multiples of 32, so a warp's 32
+    // positions of one slice share one word)
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int64_t pos = base + static_cast<int64_t>(q) * blockDim.x;
+      if (pos < n && (pos & 31) == 0) t.lost[pos >> 5] = 0u;
+    }
+  }
   if (threadIdx.x == 0) {
     int got = 0, top = 0;
     if (total > 0) {

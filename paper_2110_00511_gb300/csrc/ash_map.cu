@@ -379,6 +379,9 @@ ash_status ensure_win_bits(ash_map* m, int64_t n, cudaStream_t st) {
     return fail(ASH_ERR_OOM, "winner-flag allocation failed");
   }
   m->win_bits_bytes = want;
+  // all bits start clear; every insert's commit clears the words it read
+  ASH_CUDA(cudaMemsetAsync(m->win_bits, 0, want, st));
+  m->win_bits_clean = true;
   return ASH_OK;
 }
 
@@ -626,15 +629,14 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   if (s != ASH_OK) return s;
   s = ensure_win_bits(m, n, st);
   if (s != ASH_OK) return s;
-  ASH_CUDA(cudaMemsetAsync(m->win_bits, 0, (n + 31) / 32 * 4, st));
+  // an insert that stopped between its claim and its commit left flags set
+  if (!m->win_bits_clean) ASH_CUDA(cudaMemsetAsync(m->win_bits, 0, m->win_bits_bytes, st));
+  m->win_bits_clean = false;  // until every commit of this insert is enqueued
   const ash::Launch L = launch_of(m, st);
   ash::TableView tv = view_of(m);
-  tv.lost = m->win_bits;
   const int kpt = m->tuning.keys_per_thread;
   const int pref = claim_prefers_slot(m);
-  if (pts) m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
-  else m->K.claim(m->S, kpt, pref, tv, keys, n, idx, L);
-  if (!pref) m->pref_placed = false;  // the bucket-first claim places keys in slot order
+  const int ckpt = m->tuning.commit_keys_per_thread ? m->tuning.commit_keys_per_thread : kpt;
   // one value buffer with small rows: copied by the committing thread;
   // anything else: warp-per-row scatter after the commit
   bool inline_value = false;
@@ -659,10 +661,17 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
       }
     }
   }
-  const int ckpt = m->tuning.commit_keys_per_thread ? m->tuning.commit_keys_per_thread : kpt;
-  if (pts) m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
-  else m->K.commit(ckpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+  tv.lost = m->win_bits;
+  if (pts) {
+    m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
+    m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
+  } else {
+    m->K.claim(m->S, kpt, pref, tv, keys, n, idx, L);
+    m->K.commit(ckpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+  }
   if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
+  if (!pref) m->pref_placed = false;  // the bucket-first claim places keys in slot order
+  m->win_bits_clean = true;  // the commits clear every winner-flag word they read
   m->size_ub += n;
   m->used_ub += n;
   m->added_since_snap += n;
@@ -756,6 +765,9 @@ ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t
     return cuda_fail(cudaGetLastError(), "ash_create");
   }
   s = alloc_storage(m, capacity, st);
+  // winner flags for a first insert of up to `capacity` keys, allocated here
+  // so that the insert itself allocates nothing
+  if (s == ASH_OK) s = ensure_win_bits(m, capacity, st);
   if (s != ASH_OK) {
     std::string msg = g_last_error;
     ash_destroy(m);
@@ -1117,10 +1129,13 @@ ash_status ash_quantize(const float* points, int64_t n_coords, float cell, int32
   return check_launch("quantize");
 }
 
-ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector_bytes, uint32_t seed,
-                                 uint32_t* sink, int64_t sink_len, ash_stream stream) {
+ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_reads, int sector_bytes,
+                                 int loads_per_thread, uint32_t seed, uint32_t* sink, int64_t sink_len,
+                                 ash_stream stream) {
   if (!buf || !sink || sink_len < 1 || n_reads < 0) return fail(ASH_ERR_INVALID, "bad probe arguments");
   if (sector_bytes != 32 && sector_bytes != 64) return fail(ASH_ERR_INVALID, "sector_bytes must be 32 or 64");
+  if (loads_per_thread != 4 && loads_per_thread != 8 && loads_per_thread != 16)
+    return fail(ASH_ERR_INVALID, "loads_per_thread must be 4, 8 or 16");
   if (buf_bytes < 64 || buf_bytes % 64 != 0) return fail(ASH_ERR_INVALID, "buf_bytes must be a positive multiple of 64");
   if ((reinterpret_cast<uintptr_t>(buf) & 63u) != 0) return fail(ASH_ERR_INVALID, "buf must be 64-byte aligned");
   int dev = 0;
@@ -1129,7 +1144,7 @@ ash_status ash_probe_random_read(const void* buf, int64_t buf_bytes, int64_t n_r
   L.stream = reinterpret_cast<cudaStream_t>(stream);
   L.block = 256;
   L.grid_cap = sm_count(dev) * 8;
-  ash::launch_probe(buf, buf_bytes, n_reads, sector_bytes, seed, sink, sink_len, L);
+  ash::launch_probe(buf, buf_bytes, n_reads, sector_bytes, loads_per_thread, seed, sink, sink_len, L);
   return check_launch("probe");
 }
 

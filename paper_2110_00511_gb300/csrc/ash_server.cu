@@ -248,6 +248,20 @@ ash_status grow_for_insert(ash_server* s, int t, int64_t n) {
   return ASH_OK;
 }
 
+}  // namespace
+
+namespace ash {
+namespace host {
+void server_layout(const ash_server* s, int* key_dim, int* value_row_bytes, int* n_tenants) {
+  *key_dim = s->cfg.key_dim;
+  *value_row_bytes = s->cfg.value_row_bytes;
+  *n_tenants = s->cfg.n_tenants;
+}
+}  // namespace host
+}  // namespace ash
+
+namespace {
+
 void worker_loop(ash_server* s) {
   DeviceGuard g(s->cfg.device);
   std::unique_lock<std::mutex> lk(s->mu);

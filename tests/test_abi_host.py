@@ -78,7 +78,8 @@ def test_geometry_and_probe_validation():
     _err(L.ash_tsdf_integrate(None, 0, 1, p, 4, p, 4, 4, intr, extr, 0.01, 0.03, 4.0, None))
     _err(L.ash_tsdf_raycast(None, 0, 1, None, intr, extr, 4, 4, 0.01, 0.3, 0.01, 10, p, None))
     _err(L.ash_probe_random_atomic(p, 64, 10, 2, 0, p, 4, None))
-    _err(L.ash_probe_random_read(p, 64, 10, 48, 0, p, 4, None))
+    _err(L.ash_probe_random_read(p, 64, 10, 48, 8, 0, p, 4, None))
+    _err(L.ash_probe_random_read(p, 64, 10, 32, 5, 0, p, 4, None))
 
 
 def test_server_config_validation():
@@ -89,3 +90,18 @@ def test_server_config_validation():
         c = ash.ash_server_default_config()
         setattr(c, field, bad)
         _err(L.ash_server_create(ctypes.byref(c), ctypes.byref(out)))
+
+
+def test_erase_noalloc_binding_rejects_bad_arrays():
+    """The Python route to ash_erase_noalloc checks its arrays before the
+    library sees them: host tensors, wrong dtypes or shapes never reach the
+    kernels (the checks run before any device work, so they hold on CPU)."""
+    import torch
+    k_cpu = torch.zeros((4, 3), dtype=torch.int32)
+    m_cpu = torch.zeros(4, dtype=torch.bool)
+    with pytest.raises(ValueError, match="CUDA"):
+        ash.ash_erase_noalloc(None, k_cpu, m_cpu)
+    with pytest.raises(ValueError, match="CUDA|int32"):
+        ash.ash_erase_noalloc(None, k_cpu.to(torch.int64), m_cpu)
+    with pytest.raises(ValueError, match="torch tensors"):
+        ash.ash_erase_noalloc(None, k_cpu.numpy(), m_cpu)

@@ -174,3 +174,20 @@ def test_all_cores_oracle_step_counts_every_point():
     own = bench._owner(keys, 4)
     assert own.min() >= 0 and own.max() < 4
     assert np.array_equal(own, bench._owner(keys.copy(), 4))
+
+
+def test_random_and_streamed_split_adds_up():
+    """The (random, streamed) splits add up to the algorithmic byte models,
+    and the random-access fraction is 1 exactly when the measured time equals
+    the probe time for the random part plus the copy time for the rest."""
+    r, s_ = bench.split_find(700, 300)
+    assert r + s_ == bench.bytes_find(700, 300)
+    assert r == 32 * 1000 + 32 * 700
+    r, s_ = bench.split_activate(1000, 600)
+    assert r + s_ == bench.bytes_claim(1000) + bench.bytes_commit(1000, 600, 0)
+    assert r == 64 * 1000 + 32 * 600
+    ms = (3.2e9 / 40e9 + 1.0e9 / 6000e9) * 1000
+    f = bench.random_access_fraction(ms, 3.2e9, 1.0e9, 40.0, 6000.0)
+    assert abs(f - 1.0) < 1e-12
+    assert bench.random_access_fraction(2 * ms, 3.2e9, 1.0e9, 40.0, 6000.0) == pytest.approx(0.5)
+    assert bench.random_access_fraction(ms, 1, 1, None, 6000.0) is None

@@ -312,6 +312,45 @@ def test_voxelization_scene():
     assert np.array_equal(uniq[np.lexsort(uniq.T[::-1])], want)
 
 
+@pytest.mark.parametrize("voxel", [0.01, 0.02, 0.05])
+def test_voxelization_voxel_sizes_full_size(voxel):
+    """The voxelization step at the paper's larger voxel sizes (Sec. 6.1), on
+    the full 4M-point scene, where many points share a voxel (about 15 per
+    voxel at 50 mm): the activated key set is np.unique of the keys, the
+    winners are exactly the first occurrences, every point finds the index
+    its voxel's first point received, and at 50 mm the insert with point-id
+    values matches the oracle entry for entry."""
+    pts = workloads.voxel_scene_points(n=4_000_000, seed=0)
+    n = pts.shape[0]
+    okeys = oracle.quantize(pts, voxel)
+    gkeys = ash.ash_quantize(dev(pts), voxel).reshape(n, 3)
+    assert np.array_equal(gkeys.cpu().numpy(), okeys)
+    want, first, inverse = np.unique(okeys, axis=0, return_index=True, return_inverse=True)
+    inverse = inverse.reshape(-1)
+    hm = ash.HashMap(3, n, [(1,)], [torch.int32])
+    gi, gm = hm.insert(gkeys, [torch.arange(n, dtype=torch.int32, device="cuda")])
+    wmask = np.zeros(n, bool)
+    wmask[first] = True
+    assert np.array_equal(gm.cpu().numpy(), wmask)
+    assert hm.size() == len(want)
+    act = hm.active_indices()
+    uniq = hm.gather_keys(act).cpu().numpy()
+    assert np.array_equal(uniq[np.lexsort(uniq.T[::-1])], want)
+    fi, fm = hm.find(gkeys)
+    assert bool(fm.all())
+    gi_np = gi.cpu().numpy()
+    assert np.array_equal(fi.cpu().numpy(), gi_np[first[inverse]])
+    # the stored value of each voxel is its first point's id
+    v = hm.value_buffer(0)[fi.long()].reshape(-1).cpu().numpy()
+    assert np.array_equal(v, first[inverse].astype(np.int32))
+    if voxel == 0.05:
+        om = oracle.OracleMap(3, n, [4])
+        oi, omask = om.insert(okeys, [np.arange(n, dtype=np.int32)])
+        assert_op_parity(hm, okeys, gi, gm, oi, omask)
+        assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
 @pytest.mark.parametrize("rho", [0.1, 0.5, 1.0])
 def test_uniqueness_sweep_1e6(rho):
     keys = workloads.uniform_keys(1_000_000, rho, seed=3)
@@ -727,3 +766,4 @@ def test_point_input_ops(d, cell):
     aoi, aom = os_.activate(keys)
     assert_op_parity(hs, keys, ai, am, aoi, aom)
     assert_same_map(hs, os_)
+

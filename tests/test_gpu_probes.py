@@ -64,7 +64,8 @@ def test_read_probe_runs_on_both_sector_sizes():
     buf = torch.zeros(1 << 22, dtype=torch.uint8, device="cuda")
     sink = torch.zeros(64, dtype=torch.int32, device="cuda")
     for sector in (32, 64):
-        ash.ash_probe_random_read(buf, 1 << 16, sector, sink, seed=1)
+        for loads in (4, 8, 16):
+            ash.ash_probe_random_read(buf, (1 << 16) + 3, sector, sink, seed=1, loads_per_thread=loads)
     torch.cuda.synchronize()
     # zero-filled input never matches the sink's trigger value
     assert torch.all(sink == 0)

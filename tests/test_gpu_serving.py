@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from parity import assert_same_map
+from parity import assert_same_map, gpu_state, oracle_state
 from paper_2110_00511_gb300 import ash
 
 pytestmark = pytest.mark.gpu
@@ -152,3 +152,57 @@ def test_server_rejects_bad_requests():
     with pytest.raises(ash.AshError):
         srv.wait(rid)  # already collected
     srv.close()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_native_replay_matches_sequential_calls(mode):
+    """The native replays used by the bench: one Poisson trace through the
+    server (from native threads) and as sequential plain calls leaves every
+    tenant's map with the same key -> value dictionary (each tenant's
+    requests apply in arrival order in both), every request completes, and
+    the sequential maps equal the oracle run on the same trace.  Malformed
+    traces are refused before anything runs."""
+    rng = np.random.default_rng(40 + mode)
+    n_t, R, rows = 4, 300, 200_000
+    keys = torch.from_numpy(rng.integers(-50, 50, size=(rows, 3)).astype(np.int32)).pin_memory().numpy()
+    vals = torch.from_numpy(rng.random(rows, dtype=np.float32)).pin_memory().numpy()
+    sizes = np.exp(rng.uniform(np.log(100), np.log(20_000), size=R)).astype(np.int64)
+    trace = ash.Trace(np.cumsum(rng.exponential(1 / 20_000.0, size=R)), rng.integers(0, n_t, size=R),
+                      np.array([ash.ASH_OP_INSERT, ash.ASH_OP_FIND, ash.ASH_OP_ERASE])[rng.choice(3, size=R, p=[.4, .45, .15])],
+                      sizes, rng.integers(0, rows - sizes), keys, vals)
+    srv = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=1 << 12, value_row_bytes=4, staging_bytes=8 << 20,
+                     zero_copy=mode)
+    lat, span = srv.replay(trace, threads=4)
+    assert np.all(lat >= 0) and span > 0
+    maps = [ash.HashMap(3, 1 << 12, [(1,)], [torch.float32]) for _ in range(n_t)]
+    slat, sspan = ash.replay_sequential(maps, trace)
+    assert np.all(slat >= 0) and sspan > 0
+    oms = [oracle.OracleMap(3, 1 << 12, [4]) for _ in range(n_t)]
+    for r in range(R):
+        k = keys[trace.row[r]:trace.row[r] + trace.n[r]]
+        om = oms[trace.tenant[r]]
+        if trace.op[r] == ash.ASH_OP_INSERT:
+            om.insert(k, [vals[trace.row[r]:trace.row[r] + trace.n[r]]])
+        elif trace.op[r] == ash.ASH_OP_FIND:
+            om.find(k)
+        else:
+            om.erase(k)
+    torch.cuda.synchronize()
+    for t in range(n_t):
+        assert_same_map(maps[t], oms[t])
+        # the server grows at load 0.7, so only its capacity may differ from the oracle's
+        served = ash.HashMap.wrap(srv.map_handle(t), 3, [(1,)], [torch.float32])
+        gk, gv = gpu_state(served)
+        ok, ov = oracle_state(oms[t])
+        assert np.array_equal(gk, ok) and all(np.array_equal(a, b) for a, b in zip(gv, ov))
+        assert served.size() == oms[t].size()
+    srv.close()
+    bad = ash.Trace(np.array([0.0, 0.0]), np.array([0, 9]), np.array([2, 2]), np.array([10, 10]), np.array([0, 0]),
+                    keys, vals)
+    srv2 = ash.Server(n_tenants=n_t, key_dim=3, initial_capacity=1 << 12, value_row_bytes=4)
+    with pytest.raises(ash.AshError):
+        srv2.replay(bad)
+    past = ash.Trace(np.array([0.0]), np.array([0]), np.array([2]), np.array([10]), np.array([rows - 5]), keys, vals)
+    with pytest.raises(ash.AshError):
+        ash.replay_sequential(maps, past)
+    srv2.close()

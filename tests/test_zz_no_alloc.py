@@ -75,3 +75,19 @@ def test_noalloc_erase_at_the_limit_and_beyond(ash_mod):
         ash_mod.ash_erase_noalloc(b.handle, too_many, out)
     assert e.value.status == ash_mod.ASH_ERR_INVALID
     assert "ASH_ERASE_NOALLOC_MAX_KEYS" in str(e.value)
+
+
+def test_noalloc_erase_binding_checks_outputs(ash_mod):
+    """Short or mistyped output arrays are refused before any kernel runs,
+    and the map-level method gives the same masks as HashMap.erase."""
+    keys = torch.zeros((8, 3), dtype=torch.int32, device="cuda")
+    a, b = _twin_maps(ash_mod, keys, torch.zeros(8, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError, match="at least n"):
+        ash_mod.ash_erase_noalloc(b.handle, keys, torch.empty(7, dtype=torch.bool, device="cuda"))
+    with pytest.raises(ValueError, match="bool or uint8"):
+        ash_mod.ash_erase_noalloc(b.handle, keys, torch.empty(8, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError, match="key_dim"):
+        ash_mod.ash_erase_noalloc(b.handle, torch.zeros((8, 2), dtype=torch.int32, device="cuda"),
+                                  torch.empty(8, dtype=torch.bool, device="cuda"))
+    assert torch.equal(a.erase(keys), b.erase_noalloc(keys))
+    assert a.size() == b.size() == 0
