@@ -1146,6 +1146,80 @@ def probe_random_gbs(buf_bytes, device, reps=3):
     return n_reads * 32 / (best / 1000.0) / 1e9, n_reads / (best / 1000.0) / 1e9
 
 
+def small_call_figures(keys, queries, n, device, flush, calls=64):
+    """Per-call cost of small batches, three ways (microseconds):
+      python:    CUDA events around one HashMap call (host time of the
+                 binding and the library included, as the sweep times it);
+      abi:       events around one call of the C ABI with outputs allocated
+                 beforehand (the library's host time and its kernels);
+      pipelined: `calls` calls issued back to back through HashMap (activate
+                 on as many fresh maps, find on one map), total time / calls:
+                 the cost per call when the host keeps the stream busy."""
+    import torch
+    from paper_2110_00511_gb300 import ash
+    L = ash.lib()
+    idx = torch.empty(n, dtype=torch.int32, device=device)
+    msk = torch.empty(n, dtype=torch.bool, device=device)
+    st = ash._stream_of(device.index)
+
+    def ev_span(fn, reps=5):
+        best = None
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        return 1000.0 * best
+
+    out = {}
+    fresh = []
+
+    def fresh_map():
+        fresh.append(ash.HashMap(3, n, device=device))
+        torch.cuda.synchronize()
+        return fresh[-1]
+
+    res = {}
+    for name in ("python", "abi"):
+        best = None
+        for _ in range(5):
+            m = fresh_map()
+            if name == "python":
+                us = ev_span(lambda: m.activate(keys), reps=1)
+            else:
+                us = ev_span(lambda: L.ash_activate(m.handle, keys.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st),
+                             reps=1)
+            best = us if best is None else min(best, us)
+        res[name] = best
+    maps = [ash.HashMap(3, n, device=device) for _ in range(calls)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for m in maps:
+        m.activate(keys)
+    e1.record()
+    torch.cuda.synchronize()
+    res["pipelined"] = 1000.0 * e0.elapsed_time(e1) / calls
+    out["activate_us"] = res
+    m = maps[0]
+    res = {"python": ev_span(lambda: m.find(queries)),
+           "abi": ev_span(lambda: L.ash_find(m.handle, queries.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st))}
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(calls):
+        m.find(queries)
+    e1.record()
+    torch.cuda.synchronize()
+    res["pipelined"] = 1000.0 * e0.elapsed_time(e1) / calls
+    out["find_us"] = res
+    del maps, fresh
+    return out
+
+
 def sweep_figures(args, device, hbm_peak):
     """The uniqueness sweep of the voxelization setting (Sec. 5.1 / 6.1
     shape): n uniform int32x3 keys at uniqueness rho, capacity n, activate of
@@ -1205,6 +1279,7 @@ def sweep_figures(args, device, hbm_peak):
             hm = holder["hm"]
             n_unique = hm.size()
             ms_find = timed(lambda _: hm.find(queries))
+        small = small_call_figures(keys, queries, n, device, flush) if n <= 100_000 else None
         t = hm.tuning()
         slots = int(n * t.slots_per_capacity)
         # the random accesses touch one 32 B bucket per distinct key and its
@@ -1228,6 +1303,8 @@ def sweep_figures(args, device, hbm_peak):
                          "random_bytes": rnd, "streamed_bytes": stm,
                          "random_Gsectors": rnd / 32 / (ms / 1000.0) / 1e9,
                          "frac_random_access_roofline": random_access_fraction(ms, rnd, stm, r_gbs, hbm_peak)}
+        if small is not None:
+            rec["per_call"] = small
         out["points"].append(rec)
         del hm, keys, queries
         holder.clear()
@@ -1655,7 +1732,7 @@ def serving_figures(args, device, n_tenants=16, clients=8):
 
     for ri, rate in enumerate(rates):
         runs = {k: [] for k in list(forms) + ["sequential_plain"]}
-        batches = {k: [0, 0, 0] for k in forms}
+        batches = {k: [0, 0, 0, 0, 0] for k in forms}
         offered = []
         for rep in range(reps):
             tr = make_trace(rate, 100 + 10 * ri + rep)
@@ -1666,9 +1743,13 @@ def serving_figures(args, device, n_tenants=16, clients=8):
                 lat, span = srv.replay(tr, clients)
                 st1 = srv.stats()
                 runs[name].append(summarize(lat, keys_total, span))
+                print(f"serving {int(rate)} rep {rep} {name}: {len(lat) / span:.0f} req/s p99 "
+                      f"{np.percentile(lat, 99):.2f} ms", file=sys.stderr, flush=True)
                 batches[name][0] += st1["batches"] - st0["batches"]
                 batches[name][1] += st1["batched_requests"] - st0["batched_requests"]
                 batches[name][2] += st1["rehashes"] - st0["rehashes"]
+                batches[name][3] += st1["host_syncs"] - st0["host_syncs"]
+                batches[name][4] += st1["pinned_spills"] - st0["pinned_spills"]
             lat, span = ash.replay_sequential(maps, tr)
             runs["sequential_plain"].append(summarize(lat, keys_total, span))
         entry = {"offered_keys_per_s": float(np.median(offered))}
@@ -1679,9 +1760,11 @@ def serving_figures(args, device, n_tenants=16, clients=8):
                 agg[k] = float(np.median(vals))
                 agg[k + "_range"] = [float(min(vals)), float(max(vals))]
             if name in batches:
-                nb, nr, nrh = batches[name]
+                nb, nr, nrh, nsync, nspill = batches[name]
                 agg["avg_requests_per_batch"] = nr / max(1, nb)
                 agg["growth_rehashes"] = nrh
+                agg["host_syncs"] = nsync
+                agg["pinned_spills"] = nspill
             entry[name] = agg
         out["rates"][str(int(rate))] = entry
     for srv in forms.values():

@@ -77,7 +77,10 @@ typedef struct ash_tuning {
   int32_t blocks_per_sm;      /* grid = SM count x blocks_per_sm (grid-stride loops) */
   int32_t max_probes;         /* bucket probes before a key fails; 0 = every bucket */
   int32_t auto_grow;          /* 1: insert/activate double the capacity until size+n <= c (Sec. 4.5) */
-  float max_used_fraction;    /* rebuild the table when live+erased slots would pass this fraction */
+  float max_used_fraction;    /* rebuild the table when live+erased slots would pass this fraction
+                                 (0.65: erased slots stay as tombstones until a rebuild, and with
+                                 linear bucket probing a lookup that misses walks 1.5 buckets on
+                                 average at 0.6 of the slots used but 6 at 0.85) */
   int32_t inline_value_bytes; /* a map with ONE value buffer whose rows are 4, 8 or 16 bytes (at most
                                  this limit, both bases aligned to the row size) has them copied by
                                  the committing thread; other layouts use a warp-per-row scatter
@@ -347,13 +350,17 @@ ash_status ash_autotune(int key_dim, int64_t capacity, float rho, int device, as
  * requests in arrival order while their device staging fits staging_bytes,
  * batches at most one request per tenant (so each tenant's requests apply in
  * arrival order), grows a tenant map x2 before an insert would push its
- * live/capacity ratio past max_load, and runs each batch as one
- * ash_batch_run graph between an upload and a download on separate streams.
+ * live/capacity ratio past max_load (and rebuilds its table when erased
+ * slots would pass the map's max_used_fraction) on a growth stream, leaving
+ * that tenant out of batches until the growth finishes, and runs each batch
+ * as one ash_batch_run graph between an upload and a download on separate
+ * streams.
  * Requests that arrive while batches are on the GPU join the next batch.
  *   ash_server_wait: blocks until the request's outputs are on the host,
- *     copies them to the caller's buf_indices/masks (given at submit; they
- *     must stay valid until then) and returns the latency from submit to
- *     outputs on the host.  timeout_ms < 0 waits forever; a timeout returns
+ *     in the caller's buf_indices/masks (given at submit; they must stay
+ *     valid until then: page-locked output arrays receive the outputs by DMA,
+ *     others by a copy from pinned staging here) and returns the latency from
+ *     submit to outputs on the host.  timeout_ms < 0 waits forever; a timeout returns
  *     ASH_ERR_TIMEOUT and the request can be waited for again.
  *   ash_server_map / ash_server_stream: a tenant map and the stream its
  *     kernels run on, for inspection after all submitted requests were
@@ -389,6 +396,8 @@ typedef struct ash_server_stats {
   int64_t batches;
   int64_t batched_requests;
   int64_t rehashes;
+  int64_t host_syncs;     /* growth checks of tenant maps that had to synchronise a stream */
+  int64_t pinned_spills;  /* host staging blocks pinned during serving (the arena was full) */
 } ash_server_stats;
 void ash_server_default_config(ash_server_config* out);
 ash_status ash_server_create(const ash_server_config* cfg_host, ash_server** out_host);
@@ -408,8 +417,9 @@ ash_status ash_server_stream(ash_server* server, ash_stream* out_host);
  * ([rows, key_dim] int32, host memory; pinned arrays let zero_copy mode 2
  * upload them by DMA) and, for inserts, the same rows of values_host
  * ([rows] value rows).  arrival_s[r] is its arrival time in seconds after
- * the start (non-decreasing).  Outputs go to host arrays the replay recycles
- * by size class.
+ * the start (non-decreasing).  ash_server_replay lays out every request's
+ * outputs in one page-locked host arena before the replay starts (kept for
+ * later replays until the process exits); one replay runs at a time.
  *   ash_server_replay: `threads` submitter threads submit request r (r mod
  *     threads) at its arrival time, one tenant's requests in trace order
  *     (a request waits for the submit of its tenant's previous one); as

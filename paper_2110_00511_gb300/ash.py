@@ -62,7 +62,8 @@ class ServerConfig(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
-                ("batched_requests", ctypes.c_int64), ("rehashes", ctypes.c_int64)]
+                ("batched_requests", ctypes.c_int64), ("rehashes", ctypes.c_int64), ("host_syncs", ctypes.c_int64),
+                ("pinned_spills", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -73,6 +73,7 @@ struct ash_map {
   // rehash until the first erase (growth keeps it).  Commit skips the heap
   // read and the listing writes 0..t-1.
   bool heap_identity = true;
+  int64_t host_syncs = 0;          // growth checks that synchronised a stream (refresh)
   ash_tuning tuning{};
   ash::DimKernels K{};
   ash::host::Allocator alloc;

@@ -234,6 +234,7 @@ int64_t slots_for(int64_t capacity, const ash_tuning& t) {
 
 // Reads the control block (synchronises `st`).
 ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int* status) {
+  __atomic_fetch_add(&m->host_syncs, 1, __ATOMIC_RELAXED);  // read by other threads as a statistic
   ASH_CUDA(cudaMemcpyAsync(m->ctrl_host, m->ctrl, sizeof(ash::Ctrl), cudaMemcpyDeviceToHost, st));
   ASH_CUDA(cudaStreamSynchronize(st));
   const unsigned long long tu = m->ctrl_host->top_used;
@@ -695,7 +696,7 @@ void ash_default_tuning(ash_tuning* out) {
   out->blocks_per_sm = 8;
   out->max_probes = 0;
   out->auto_grow = 1;
-  out->max_used_fraction = 0.85f;
+  out->max_used_fraction = 0.65f;
   out->inline_value_bytes = 16;
   out->keys_per_thread = 2;
   out->warp_probe = 0;

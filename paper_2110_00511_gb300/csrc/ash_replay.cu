@@ -26,47 +26,49 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-// Host output arrays (indices then masks) recycled by size class, as a
-// serving frontend would keep them.
-class OutPool {
- public:
-  char* take(int64_t n) {
-    const int64_t cls = size_class(n);
-    {
-      std::lock_guard<std::mutex> lk(mu_);
-      auto& v = free_[cls];
-      if (!v.empty()) {
-        char* p = v.back();
-        v.pop_back();
-        return p;
-      }
-    }
-    char* p = static_cast<char*>(std::malloc(static_cast<size_t>(cls)));
-    if (p) {
-      std::lock_guard<std::mutex> lk(mu_);
-      all_.push_back(p);
-    }
-    return p;
-  }
-  void give(char* p, int64_t n) {
-    std::lock_guard<std::mutex> lk(mu_);
-    free_[size_class(n)].push_back(p);
-  }
-  ~OutPool() {
-    for (char* p : all_) std::free(p);
-  }
-
- private:
-  static int64_t size_class(int64_t n) {
-    int64_t b = 4096;
-    const int64_t need = n * 5 + 16;
-    while (b < need) b *= 2;
-    return b;
-  }
-  std::mutex mu_;
-  std::map<int64_t, std::vector<char*>> free_;
-  std::vector<char*> all_;
+// Host output arrays (indices, then masks) for every request of a trace, in
+// one page-locked arena laid out before the replay starts, as a serving
+// frontend with pinned buffers would hold them: the server downloads
+// outputs into them by DMA, and no allocation falls inside the measured
+// time.  The arena is kept for the next replay of the process (grown when a
+// trace needs more) and is never freed: the CUDA runtime may be gone at
+// exit.
+struct OutArena {
+  std::mutex mu;
+  char* base = nullptr;
+  int64_t bytes = 0;
 };
+
+OutArena& out_arena() {
+  static OutArena* a = new OutArena();
+  return *a;
+}
+
+// Offsets of each request's outputs (16-byte aligned: n int32 indices, then
+// n mask bytes) and the arena holding them, or nullptr when pinning failed.
+char* layout_outputs(const ash_replay_trace* t, std::vector<int64_t>& off) {
+  off.resize(static_cast<size_t>(t->n_requests));
+  int64_t at = 0;
+  for (int64_t r = 0; r < t->n_requests; ++r) {
+    off[static_cast<size_t>(r)] = at;
+    at += (t->n[r] * 5 + 15) / 16 * 16;
+  }
+  OutArena& a = out_arena();
+  if (a.bytes < at) {
+    if (a.base) cudaFreeHost(a.base);
+    a.base = nullptr;
+    a.bytes = 0;
+    const int64_t want = at + at / 4;  // headroom: traces of one workload differ a little in size
+    void* p = nullptr;
+    if (cudaMallocHost(&p, static_cast<size_t>(want)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    a.base = static_cast<char*>(p);
+    a.bytes = want;
+  }
+  return a.base;
+}
 
 ash_status check_trace(const ash_replay_trace* t, int n_tenants) {
   if (!t || t->n_requests < 0) return fail(ASH_ERR_INVALID, "trace is required");
@@ -117,9 +119,11 @@ ash_status ash_server_replay(ash_server* server, const ash_replay_trace* trace, 
       last[static_cast<size_t>(trace->tenant[r])] = r;
     }
   }
-  OutPool pool;
+  std::lock_guard<std::mutex> arena_lock(out_arena().mu);  // one replay at a time uses the arena
+  std::vector<int64_t> out_off;
+  char* arena = layout_outputs(trace, out_off);
+  if (!arena) return fail(ASH_ERR_OOM, "replay: pinned output arena allocation failed");
   std::vector<std::atomic<uint64_t>> rid(static_cast<size_t>(R));
-  std::vector<char*> out(static_cast<size_t>(R), nullptr);
   for (auto& x : rid) x.store(0, std::memory_order_relaxed);
   std::atomic<int> error{ASH_OK};
   std::atomic<int64_t> last_done_ns{0};
@@ -136,22 +140,19 @@ ash_status ash_server_replay(ash_server* server, const ash_replay_trace* trace, 
         while (rid[static_cast<size_t>(p)].load(std::memory_order_acquire) == 0)
           std::this_thread::sleep_for(std::chrono::microseconds(2));
       const int64_t n = trace->n[r];
-      char* o = error.load() == ASH_OK ? pool.take(n) : nullptr;
+      char* o = arena + out_off[static_cast<size_t>(r)];
       uint64_t id = 0;
-      ash_status st = ASH_ERR_OOM;
-      if (o) {
+      ash_status st = static_cast<ash_status>(error.load());
+      if (st == ASH_OK) {
         const int32_t* k = trace->keys_host + trace->row[r] * key_dim;
         const void* v = (trace->op[r] == ASH_OP_INSERT && value_row_bytes > 0) ? vals + trace->row[r] * value_row_bytes
                                                                                 : nullptr;
         st = ash_server_submit(server, trace->tenant[r], trace->op[r], k, v, n, reinterpret_cast<int32_t*>(o),
                                reinterpret_cast<uint8_t*>(o + 4 * n), &id);
       }
-      out[static_cast<size_t>(r)] = o;
       if (st != ASH_OK) {
         int ok = ASH_OK;
         error.compare_exchange_strong(ok, st);
-        if (o) pool.give(o, n);
-        out[static_cast<size_t>(r)] = nullptr;
         rid[static_cast<size_t>(r)].store(kFailed, std::memory_order_release);
       } else {
         rid[static_cast<size_t>(r)].store(id, std::memory_order_release);
@@ -176,7 +177,6 @@ ash_status ash_server_replay(ash_server* server, const ash_replay_trace* trace, 
       }
       const auto due = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(trace->arrival_s[r]));
       latency_ms_host[r] = ms_between(due, now);
-      pool.give(out[static_cast<size_t>(r)], trace->n[r]);
       const int64_t ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - t0).count();
       int64_t prev = last_done_ns.load();
       while (ns > prev && !last_done_ns.compare_exchange_weak(prev, ns)) {

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -63,6 +64,10 @@ class PinnedPool {
     free_.emplace(0, bytes);
   }
   void* take(int64_t bytes, int64_t* cls_bytes) {
+    if (bytes <= 0) {
+      *cls_bytes = 0;
+      return nullptr;
+    }
     const int64_t need = (bytes + kUnit - 1) / kUnit * kUnit;
     {
       std::lock_guard<std::mutex> lk(mu_);
@@ -74,24 +79,34 @@ class PinnedPool {
         *cls_bytes = need;  // arena block: its size
         return base_ + off;
       }
-      auto& v = spill_[need];
+      // spill blocks come in power-of-two sizes, so that the few classes
+      // are reused instead of pinning a new block of every request size
+      auto& v = spill_[spill_class(need)];
       if (!v.empty()) {
         void* p = v.back();
         v.pop_back();
-        *cls_bytes = -need;  // spill block
+        *cls_bytes = -spill_class(need);  // spill block
         return p;
       }
     }
+    const int64_t cls = spill_class(need);
     void* p = nullptr;
-    if (cudaMallocHost(&p, need) != cudaSuccess) {
+    if (cudaMallocHost(&p, cls) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    *cls_bytes = -need;
+    spills_.fetch_add(1, std::memory_order_relaxed);
+    *cls_bytes = -cls;
     return p;
   }
+  static int64_t spill_class(int64_t need) {
+    int64_t c = kUnit;
+    while (c < need) c *= 2;
+    return c;
+  }
+  int64_t spills() const { return spills_.load(std::memory_order_relaxed); }
   void give(void* p, int64_t cls_bytes) {
-    if (!p) return;
+    if (!p || cls_bytes == 0) return;
     std::lock_guard<std::mutex> lk(mu_);
     if (cls_bytes < 0) {
       spill_[-cls_bytes].push_back(p);
@@ -121,6 +136,7 @@ class PinnedPool {
 
  private:
   static constexpr int64_t kUnit = 4096;
+  std::atomic<int64_t> spills_{0};
   std::mutex mu_;
   char* base_ = nullptr;
   int64_t size_ = 0;
@@ -150,6 +166,7 @@ struct Request {
   const void* vals_user = nullptr;
   bool zero_copy = false;
   bool direct_in = false;    // inputs uploaded by DMA from the caller's pinned arrays
+  bool direct_out = false;   // outputs downloaded by DMA into the caller's pinned arrays
   int64_t host_out_off = 0;  // offset of the outputs in the host staging block
   // staging: [keys | values | idx | mask], each 256-byte aligned
   int64_t off_keys = 0, off_vals = 0, off_idx = 0, off_mask = 0, bytes = 0;
@@ -180,8 +197,9 @@ struct ash_server {
   std::vector<ash_map*> maps;
   ash_batch* batch = nullptr;
   cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
-  // Tenant growth runs on its own stream: only batches that include the
-  // growing tenant wait for it (grow_done[t]); the others keep running.
+  // Tenant growth runs on its own stream; the worker leaves the growing
+  // tenant out of batches until grow_done[t] has completed, so the other
+  // tenants' batches keep running.
   cudaStream_t s_grow = nullptr;
   cudaEvent_t comp_mark = nullptr;
   std::vector<cudaEvent_t> grow_done;
@@ -227,24 +245,34 @@ void CUDART_CB on_batch_done(void* arg) {
 // fits) when the host's upper bound on its live entries would pass max_load
 // of the capacity.  The growth runs on the device with no host
 // synchronisation (grow_async), on the growth stream after the compute
-// stream's work so far (which may still read the old table); the tenant's
-// next batch waits for it, other tenants' batches do not.
+// stream's work so far (which may still read the old table); the worker
+// leaves the tenant out of batches until it has finished, while other
+// tenants' batches keep running.
 ash_status grow_for_insert(ash_server* s, int t, int64_t n) {
   ash_map* m = s->maps[t];
   const double lim = s->cfg.max_load;
-  if (static_cast<double>(m->size_ub + n) > lim * static_cast<double>(m->capacity)) tighten_bounds(m);
+  const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
+  if (static_cast<double>(m->size_ub + n) > lim * static_cast<double>(m->capacity) || m->used_ub + n > max_used)
+    tighten_bounds(m);
   const double need = static_cast<double>(m->size_ub + n);
-  if (need <= lim * static_cast<double>(m->capacity)) return ASH_OK;
+  // a table whose live + erased slots could pass max_used_fraction is rebuilt
+  // here too (at the same capacity when the live entries still fit), so the
+  // batch's own growth check never has to synchronise the compute stream
+  const bool grow = need > lim * static_cast<double>(m->capacity);
+  const bool rebuild = m->used_ub + n > max_used;
+  if (!grow && !rebuild) return ASH_OK;
+  // the new capacity holds the live entries and this insert under both
+  // limits, so a rebuild is never followed by another one for the same batch
+  const double used_frac = m->tuning.max_used_fraction * m->tuning.slots_per_capacity;
   int64_t c = m->capacity;
-  while (need > lim * static_cast<double>(c)) c *= 2;
+  while (need > lim * static_cast<double>(c) || need > used_frac * static_cast<double>(c)) c *= 2;
   if (cudaEventRecord(s->comp_mark, s->s_comp) != cudaSuccess ||
       cudaStreamWaitEvent(s->s_grow, s->comp_mark, 0) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "server growth ordering");
   ash_status st = grow_async(m, c, s->s_grow);
   if (st != ASH_OK) return st;
   if (cudaEventRecord(s->grow_done[t], s->s_grow) != cudaSuccess) return cuda_fail(cudaGetLastError(), "grow event");
-  s->growing[t] = 1;
-  s->stats.rehashes += 1;
+  s->growing[t] = 1;  // the caller counts the growth in the stats
   return ASH_OK;
 }
 
@@ -264,17 +292,19 @@ namespace {
 
 void worker_loop(ash_server* s) {
   DeviceGuard g(s->cfg.device);
+  // No CUDA call is made while holding s->mu: the completion callback of a
+  // batch takes that mutex on the driver's callback thread.  growing[] and
+  // the growth events belong to this thread alone.
+  std::vector<Batch*> finished;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    // 1) release the device staging of finished batches (in order)
+    // 1) batches that finished: their device staging is released below
     while (!s->inflight.empty() && s->inflight.front()->done) {
-      Batch* b = s->inflight.front();
+      finished.push_back(s->inflight.front());
       s->inflight.pop_front();
-      for (char* p : b->dev) cudaFreeAsync(p, s->s_d2h);
-      s->staged_bytes -= b->staged;
-      delete b;
+      s->staged_bytes -= finished.back()->staged;
     }
-    if (s->stop && s->pending.empty() && s->admitted.empty() && s->inflight.empty()) break;
+    if (s->stop && s->pending.empty() && s->admitted.empty() && s->inflight.empty() && finished.empty()) break;
     // 2) admission under the HBM staging budget, in arrival order
     while (!s->pending.empty()) {
       Request* r = s->pending.front();
@@ -284,35 +314,80 @@ void worker_loop(ash_server* s) {
       s->staged_bytes += r->bytes;
       s->admitted.push_back(r);
     }
-    // 3) a batch: the oldest admitted request of each tenant
+    // 3) a batch: the oldest admitted request of each tenant.  A tenant whose
+    //    map is growing (or rebuilding) on the growth stream is left out
+    //    until that finishes, so its growth holds up no other tenant's batch.
     std::vector<Request*> pick;
+    bool any_growing = false;
     {
       bool used[kMaxTenants] = {};
+      for (int t = 0; t < s->cfg.n_tenants; ++t)
+        if (s->growing[t]) used[t] = any_growing = true;
       for (auto it = s->admitted.begin(); it != s->admitted.end() && static_cast<int>(pick.size()) < s->cfg.max_batch_requests;) {
         Request* r = *it;
-        if (!used[r->tenant]) {
-          used[r->tenant] = true;
-          pick.push_back(r);
-          it = s->admitted.erase(it);
-        } else {
+        if (used[r->tenant]) {
           ++it;
+          continue;
         }
+        used[r->tenant] = true;
+        pick.push_back(r);
+        it = s->admitted.erase(it);
       }
     }
-    if (pick.empty()) {
-      s->cv_work.wait(lk);
+    if (pick.empty() && finished.empty()) {
+      if (any_growing) {
+        s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        lk.unlock();
+        for (int t = 0; t < s->cfg.n_tenants; ++t) {  // poll the growth events
+          if (!s->growing[t]) continue;
+          if (cudaEventQuery(s->grow_done[t]) == cudaSuccess) s->growing[t] = 0;
+          else cudaGetLastError();  // cudaErrorNotReady is not an error here
+        }
+        lk.lock();
+      } else {
+        s->cv_work.wait(lk);
+      }
       continue;
     }
     lk.unlock();
-    // 4) launch: upload, one batched graph, download, host callback
+    for (Batch* b : finished) {
+      for (char* p : b->dev) cudaFreeAsync(p, s->s_d2h);
+      delete b;
+    }
+    finished.clear();
+    for (int t = 0; t < s->cfg.n_tenants; ++t) {  // growths that finished
+      if (!s->growing[t]) continue;
+      if (cudaEventQuery(s->grow_done[t]) == cudaSuccess) s->growing[t] = 0;
+      else cudaGetLastError();
+    }
+    // an insert that needs its tenant to grow starts the growth and goes back
+    // to the front of the queue (still the oldest of its tenant)
     ash_status st = ASH_OK;
-    std::vector<ash_batch_op> ops;
-    for (Request* r : pick) {
+    std::vector<Request*> deferred;
+    for (size_t j = 0; j < pick.size() && st == ASH_OK;) {
+      Request* r = pick[j];
       if (r->op == ASH_OP_INSERT || r->op == ASH_OP_ACTIVATE) {
         st = grow_for_insert(s, r->tenant, r->n);
-        if (st != ASH_OK) break;
+        if (st == ASH_OK && s->growing[r->tenant]) {
+          deferred.push_back(r);
+          pick.erase(pick.begin() + static_cast<std::ptrdiff_t>(j));
+          continue;
+        }
       }
+      ++j;
     }
+    if (!deferred.empty()) {
+      lk.lock();
+      s->admitted.insert(s->admitted.begin(), deferred.begin(), deferred.end());
+      s->stats.rehashes += static_cast<int64_t>(deferred.size());  // one growth started per deferred request
+      lk.unlock();
+    }
+    if (pick.empty() && st == ASH_OK) {
+      lk.lock();
+      continue;
+    }
+    // 4) launch: upload, one batched graph, download, host callback
+    std::vector<ash_batch_op> ops;
     if (st == ASH_OK) {
       for (Request* r : pick) {
         if (r->zero_copy) {
@@ -359,18 +434,18 @@ void worker_loop(ash_server* s) {
       cudaEventCreateWithFlags(&comp, cudaEventDisableTiming);
       cudaEventRecord(up, s->s_h2d);
       cudaStreamWaitEvent(s->s_comp, up, 0);
-      for (Request* r : pick) {
-        if (s->growing[r->tenant]) {
-          cudaStreamWaitEvent(s->s_comp, s->grow_done[r->tenant], 0);
-          s->growing[r->tenant] = 0;
-        }
-      }
       st = ash_batch_run(s->batch, ops.data(), static_cast<int>(ops.size()), reinterpret_cast<ash_stream>(s->s_comp));
       if (st == ASH_OK) {
         cudaEventRecord(comp, s->s_comp);
         cudaStreamWaitEvent(s->s_d2h, comp, 0);
         for (Request* r : pick) {
           if (r->zero_copy) continue;  // the kernels wrote the caller's arrays
+          if (r->direct_out) {
+            if (r->op != ASH_OP_ERASE)
+              cudaMemcpyAsync(r->idx_user, r->dev + r->off_idx, r->n * 4, cudaMemcpyDeviceToHost, s->s_d2h);
+            cudaMemcpyAsync(r->mask_user, r->dev + r->off_mask, r->n, cudaMemcpyDeviceToHost, s->s_d2h);
+            continue;
+          }
           const int64_t out_bytes = r->bytes - r->off_idx;
           cudaMemcpyAsync(static_cast<char*>(r->host) + r->host_out_off, r->dev + r->off_idx, out_bytes,
                           cudaMemcpyDeviceToHost, s->s_d2h);
@@ -400,14 +475,18 @@ void worker_loop(ash_server* s) {
         }
       }
     }
+    if (st != ASH_OK) {
+      for (Request* r : pick) {
+        if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
+        r->dev = nullptr;
+      }
+    }
     lk.lock();
     if (st != ASH_OK) {
       // fail the picked requests so no waiter hangs, and give back their staging
       s->worker_error = st;
       s->worker_msg = ash_last_error();
       for (Request* r : pick) {
-        if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
-        r->dev = nullptr;
         s->staged_bytes -= r->bytes;
         r->gpu_done = true;
         r->t_done = Clock::now();
@@ -529,18 +608,24 @@ ash_status ash_server_submit(ash_server* s, int32_t tenant, int32_t op, const in
   r->off_idx = r->off_vals + align256(vb);
   r->off_mask = r->off_idx + align256(n * 4);
   r->bytes = r->off_mask + align256(n);
-  // mode 2: pinned input arrays are uploaded by DMA straight from the caller
+  // mode 2: pinned input arrays are uploaded by DMA straight from the caller.
+  // Any mode: pinned output arrays receive the outputs by DMA (the caller
+  // may not read them before wait returns, so no staging is needed).
   r->direct_in = s->cfg.zero_copy == 2 && is_pinned(keys_host) && (!vb || is_pinned(values_host));
+  r->direct_out = is_pinned(masks_host) && (op == ASH_OP_ERASE || is_pinned(buf_indices_host));
+  const int64_t in_bytes = r->direct_in ? 0 : r->off_idx;
+  const int64_t out_bytes = r->direct_out ? 0 : r->bytes - r->off_idx;
+  r->host_out_off = in_bytes;  // the host block holds the staged inputs, then the staged outputs
+  r->host = nullptr;
+  r->host_cls = 0;
+  if (in_bytes + out_bytes > 0) {
+    r->host = s->pinned.take(in_bytes + out_bytes, &r->host_cls);
+    if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
+  }
   if (r->direct_in) {
     r->keys_user = keys_host;
     r->vals_user = vb ? values_host : nullptr;
-    r->host_out_off = 0;  // the host block holds only the outputs
-    r->host = s->pinned.take(r->bytes - r->off_idx, &r->host_cls);
-    if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
   } else {
-    r->host_out_off = r->off_idx;
-    r->host = s->pinned.take(r->bytes, &r->host_cls);
-    if (!r->host) return fail(ASH_ERR_OOM, "pinned staging allocation failed");
     std::memcpy(static_cast<char*>(r->host) + r->off_keys, keys_host, kb);
     if (vb) std::memcpy(static_cast<char*>(r->host) + r->off_vals, values_host, vb);
   }
@@ -581,9 +666,11 @@ ash_status ash_server_wait(ash_server* s, uint64_t request_id, int64_t timeout_m
     return fail(werr, "the serving worker failed a batch: " + wmsg);
   }
   if (!r->zero_copy) {
-    const char* out = static_cast<char*>(r->host) + r->host_out_off;
-    if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, out, r->n * 4);
-    std::memcpy(r->mask_user, out + (r->off_mask - r->off_idx), r->n);
+    if (!r->direct_out) {
+      const char* out = static_cast<char*>(r->host) + r->host_out_off;
+      if (r->op != ASH_OP_ERASE) std::memcpy(r->idx_user, out, r->n * 4);
+      std::memcpy(r->mask_user, out + (r->off_mask - r->off_idx), r->n);
+    }
     s->pinned.give(r->host, r->host_cls);
   }
   if (latency_ms_host)
@@ -597,6 +684,9 @@ ash_status ash_server_stats_get(ash_server* s, ash_server_stats* out_host) {
   if (!s || !out_host) return fail(ASH_ERR_INVALID, "server and out are required");
   std::lock_guard<std::mutex> lk(s->mu);
   *out_host = s->stats;
+  out_host->host_syncs = 0;
+  for (ash_map* m : s->maps) out_host->host_syncs += __atomic_load_n(&m->host_syncs, __ATOMIC_RELAXED);
+  out_host->pinned_spills = s->pinned.spills();
   return ASH_OK;
 }
 
