@@ -278,6 +278,10 @@ void note_insert_stream(ash_map* m, cudaStream_t st) {
 }
 
 void maybe_snapshot(ash_map* m, cudaStream_t st) {
+  // a snapshot that has landed is folded into the bounds first, so a fresh
+  // one can be taken: the bounds then lag the device by the batches issued
+  // since the last snapshot landed, not since the first one was taken
+  if (m->snap_state != 0) tighten_bounds(m);
   if (m->snap_state != 0 || !m->snap_host || m->insert_streams_mixed || st != m->insert_stream) return;
   // Never inside a stream capture: a replayed graph would write the pinned
   // slot long after this map (and its slot) are gone.
