@@ -233,6 +233,21 @@ ash_status ash_gather_values_count(ash_map* map, int j, const int32_t* indices, 
 /* Number of live entries (the heap top t).  Synchronises the stream. */
 ash_status ash_size(ash_map* map, int64_t* size_host, ash_stream stream);
 
+/* Table health of a map: capacity, table slots, live entries (the heap top
+ * t), used slots (live entries plus tombstones: erased slots stay
+ * tombstones until a rebuild when their bucket has no EMPTY slot), growth
+ * checks that had to synchronise a stream, and table rebuilds (growth,
+ * rehash, reserve, and clean-ups of erased slots).  Synchronises the stream. */
+typedef struct ash_map_stats {
+  int64_t capacity;
+  int64_t table_slots;
+  int64_t live;
+  int64_t used_slots;
+  int64_t host_syncs;
+  int64_t rebuilds;
+} ash_map_stats;
+ash_status ash_get_map_stats(ash_map* map, ash_map_stats* out_host, ash_stream stream);
+
 /* Capacity c, key dimension, and value-buffer count. */
 int64_t ash_capacity(const ash_map* map);
 int ash_key_dim(const ash_map* map);

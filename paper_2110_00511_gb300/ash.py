@@ -77,6 +77,14 @@ class DeviceInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class MapStats(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("table_slots", ctypes.c_int64), ("live", ctypes.c_int64),
+                ("used_slots", ctypes.c_int64), ("host_syncs", ctypes.c_int64), ("rebuilds", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ReplayTrace(ctypes.Structure):
     _fields_ = [("n_requests", ctypes.c_int64), ("arrival_s", ctypes.c_void_p), ("tenant", ctypes.c_void_p),
                 ("op", ctypes.c_void_p), ("n", ctypes.c_void_p), ("row", ctypes.c_void_p), ("rows", ctypes.c_int64),
@@ -106,6 +114,7 @@ _SIGS = {
     "ash_gather_keys_count": (_I32, [_P, _P, _I64, _P, _P, _P]),
     "ash_gather_values_count": (_I32, [_P, ctypes.c_int, _P, _I64, _P, _P, _P]),
     "ash_capacity": (_I64, [_P]),
+    "ash_get_map_stats": (_I32, [_P, ctypes.POINTER(MapStats), _P]),
     "ash_key_dim": (ctypes.c_int, [_P]),
     "ash_n_values": (ctypes.c_int, [_P]),
     "ash_rehash": (_I32, [_P, _I64, _P]),
@@ -734,6 +743,13 @@ class HashMap:
 
     def capacity(self):
         return int(lib().ash_capacity(self._h))
+
+    def stats(self):
+        """Table health (synchronises): capacity, table_slots, live, used_slots
+        (live + tombstones), host_syncs, rebuilds."""
+        st = MapStats()
+        _check(lib().ash_get_map_stats(self._h, ctypes.byref(st), _stream(self.device)))
+        return st.as_dict()
 
     def rehash(self, new_capacity=0):
         ash_rehash(self._h, new_capacity, _stream(self.device))

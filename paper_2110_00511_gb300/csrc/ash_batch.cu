@@ -420,6 +420,8 @@ ash_status ash_batch_run(ash_batch* b, const ash_batch_op* ops, int n_ops, ash_s
       maybe_snapshot(ops[i].map, st);
     } else if (ops[i].op == ASH_OP_ERASE) {
       ops[i].map->heap_identity = false;
+      ops[i].map->erased_since_snap += ops[i].n;
+      maybe_snapshot(ops[i].map, st);
     }
   if (cudaEventRecord(sl.done, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventRecord");
   sl.used = true;

@@ -57,6 +57,11 @@ struct ash_map {
   cudaEvent_t snap_event = nullptr;
   int snap_state = 0;              // 0 idle, 1 in flight, 2 in flight but stale
   int64_t added_since_snap = 0;    // insert/activate keys issued after the snapshot's copy
+  // Lower bound on tombstones (used - live of the last landed snapshot):
+  // inserts never reuse a tombstone, so the count only grows until a rebuild
+  // (which resets it).  Drives the clean-up rebuilds (tombstones_need_rebuild).
+  int64_t tomb_lb = 0;
+  int64_t erased_since_snap = 0;   // erase keys issued after the last snapshot (tombstones may have formed)
   // Snapshots are taken only while every insert/activate of the map has come
   // on one stream (then stream order makes "snapshot + keys issued since" an
   // upper bound); a second stream turns them off for the map's life.
@@ -74,6 +79,7 @@ struct ash_map {
   // read and the listing writes 0..t-1.
   bool heap_identity = true;
   int64_t host_syncs = 0;          // growth checks that synchronised a stream (refresh)
+  int64_t rebuilds = 0;            // table rebuilds (rebuild_to, grow_async)
   ash_tuning tuning{};
   ash::DimKernels K{};
   ash::host::Allocator alloc;
@@ -120,6 +126,8 @@ void invalidate_snapshot(ash_map* m);
 void maybe_snapshot(ash_map* m, cudaStream_t st);
 // Records the stream of an insert/activate (snapshots need a single one).
 void note_insert_stream(ash_map* m, cudaStream_t st);
+// True when the map's known tombstones call for a table rebuild.
+bool tombstones_need_rebuild(const ash_map* m);
 // Key dimension, value row bytes and tenant count of a server.
 void server_layout(const ash_server* s, int* key_dim, int* value_row_bytes, int* n_tenants);
 

@@ -246,6 +246,7 @@ ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int
   tighten_bounds(m);  // the stream is idle: a pending snapshot has landed
   m->size_ub = *top;
   m->used_ub = *used;
+  if (*used - *top > m->tomb_lb) m->tomb_lb = *used - *top;  // exact now
   return ASH_OK;
 }
 
@@ -256,12 +257,27 @@ void tighten_bounds(ash_map* m) {
   }
   if (m->snap_state == 1) {
     const unsigned long long tu = m->snap_host->top_used;
-    const int64_t top = static_cast<int64_t>(tu & 0xFFFFFFFFull) + m->added_since_snap;
-    const int64_t used = static_cast<int64_t>(tu >> 32) + m->added_since_snap;
+    const int64_t snap_top = static_cast<int64_t>(tu & 0xFFFFFFFFull);
+    const int64_t snap_used = static_cast<int64_t>(tu >> 32);
+    const int64_t top = snap_top + m->added_since_snap;
+    const int64_t used = snap_used + m->added_since_snap;
     if (top < m->size_ub) m->size_ub = top;
     if (used < m->used_ub) m->used_ub = used;
+    if (snap_used - snap_top > m->tomb_lb) m->tomb_lb = snap_used - snap_top;
   }
   m->snap_state = 0;
+}
+
+// Erased slots whose bucket has no EMPTY slot stay tombstones, and inserts
+// claim only EMPTY slots, so under insert/erase churn the runs of full
+// buckets lengthen: measured on a 2^24-capacity map, a find of 1M keys took
+// 3x as long as on a rebuilt table with tombstones at 0.3 of the live count,
+// 14x at 1.3 and 27x at 2.0, with the used slots (0.29-0.55 of the table)
+// still below max_used_fraction.  A table whose known tombstones pass a
+// quarter of its live entries (and 1/64 of its slots) is rebuilt.
+bool tombstones_need_rebuild(const ash_map* m) {
+  const int64_t live = m->size_ub;
+  return m->tomb_lb > m->n_slots / 64 && 4 * m->tomb_lb > live;
 }
 
 void invalidate_snapshot(ash_map* m) {
@@ -292,7 +308,10 @@ void maybe_snapshot(ash_map* m, cudaStream_t st) {
   }
   if (cs != cudaStreamCaptureStatusNone) return;
   const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
-  if (2 * m->size_ub <= m->capacity && 2 * m->used_ub <= max_used) return;
+  // snapshots serve the growth check (once a bound passes half its limit)
+  // and the tombstone count (after erases on a table of some size)
+  const bool churn = m->erased_since_snap > 0 && m->n_slots >= (int64_t{1} << 16);
+  if (2 * m->size_ub <= m->capacity && 2 * m->used_ub <= max_used && !churn) return;
   if (!m->snap_event) {
     if (cudaEventCreateWithFlags(&m->snap_event, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
@@ -307,6 +326,7 @@ void maybe_snapshot(ash_map* m, cudaStream_t st) {
   }
   m->snap_state = 1;
   m->added_since_snap = 0;
+  m->erased_since_snap = 0;
 }
 
 ash_status status_from_bits(int bits) {
@@ -407,6 +427,7 @@ ash_status ensure_list_scratch(ash_map* m, cudaStream_t st) {
 // Rebuilds the table for new_capacity from the live entries (Sec. 4.5).
 // size: the exact live count (caller synchronised).
 ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream_t st) {
+  __atomic_fetch_add(&m->rebuilds, 1, __ATOMIC_RELAXED);
   const ash::Launch L = launch_of(m, st);
   // 1) collect the active indices
   int32_t* list = static_cast<int32_t*>(dev_alloc(m, std::max<int64_t>(size, 1) * 4, st));
@@ -502,6 +523,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
   dev_free(m, list, st);
   m->size_ub = size;
   m->used_ub = size;
+  m->tomb_lb = 0;
   invalidate_snapshot(m);
   return check_launch("rehash");
 }
@@ -512,6 +534,7 @@ ash_status rebuild_to(ash_map* m, int64_t new_capacity, int64_t size, cudaStream
 // used-slot count is set from it.  Buffer indices are kept.
 ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
   if (new_capacity < m->capacity) return fail(ASH_ERR_INVALID, "grow_async cannot shrink");
+  __atomic_fetch_add(&m->rebuilds, 1, __ATOMIC_RELAXED);
   const ash::Launch L = launch_of(m, st);
   const int64_t c = m->capacity;
   int32_t* list = static_cast<int32_t*>(dev_alloc(m, c * 4, st));
@@ -584,6 +607,8 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
   }
   dev_free(m, list, st);
   m->used_ub = m->size_ub;
+  m->tomb_lb = 0;
+  invalidate_snapshot(m);  // a snapshot taken before the rebuild would report its tombstones
   return check_launch("grow_async");
 }
 
@@ -592,10 +617,14 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st) {
 // slots (live + tombstones) could pass max_used_fraction.
 ash_status ensure_room(ash_map* m, int64_t n, cudaStream_t st) {
   const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
-  if (m->size_ub + n > m->capacity || m->used_ub + n > max_used) tighten_bounds(m);
+  tighten_bounds(m);  // folds in a landed snapshot (never blocks)
   const bool size_risk = m->size_ub + n > m->capacity;
   const bool used_risk = m->used_ub + n > max_used;
-  if (!size_risk && !used_risk) return ASH_OK;
+  if (!size_risk && !used_risk) {
+    // a clean-up rebuild at the same capacity, enqueued with no host sync
+    if (tombstones_need_rebuild(m)) return grow_async(m, m->capacity, st);
+    return ASH_OK;
+  }
   int64_t top, used;
   ash_status s = refresh(m, st, &top, &used, nullptr);
   if (s != ASH_OK) return s;
@@ -879,6 +908,8 @@ ash_status ash_erase(ash_map* m, const int32_t* keys, int64_t n, uint8_t* masks,
   m->K.erase_mark(m->S, tv, keys, n, m->scratch, L);
   ash::launch_erase_resolve(m->S, tv, n, m->scratch, masks, L);
   m->heap_identity = false;
+  m->erased_since_snap += n;
+  maybe_snapshot(m, st);
   return check_launch("erase");
 }
 
@@ -955,6 +986,21 @@ ash_status ash_size(ash_map* m, int64_t* size_host, ash_stream stream) {
   return ASH_OK;
 }
 
+ash_status ash_get_map_stats(ash_map* m, ash_map_stats* out, ash_stream stream) {
+  if (!m || !out) return fail(ASH_ERR_INVALID, "map and out are required");
+  DeviceGuard g(m->device);
+  int64_t top, used;
+  ash_status s = refresh(m, reinterpret_cast<cudaStream_t>(stream), &top, &used, nullptr);
+  if (s != ASH_OK) return s;
+  out->capacity = m->capacity;
+  out->table_slots = m->n_slots;
+  out->live = top;
+  out->used_slots = used;
+  out->host_syncs = __atomic_load_n(&m->host_syncs, __ATOMIC_RELAXED);
+  out->rebuilds = __atomic_load_n(&m->rebuilds, __ATOMIC_RELAXED);
+  return ASH_OK;
+}
+
 int64_t ash_capacity(const ash_map* m) { return m ? m->capacity : 0; }
 int ash_key_dim(const ash_map* m) { return m ? m->key_dim : 0; }
 int ash_n_values(const ash_map* m) { return m ? m->n_values : 0; }
@@ -1002,6 +1048,7 @@ ash_status ash_clear(ash_map* m, ash_stream stream) {
   ash::launch_set_top_used(m->ctrl, 0, 0, L);
   m->size_ub = 0;
   m->used_ub = 0;
+  m->tomb_lb = 0;
   m->pref_placed = true;
   m->heap_identity = true;
   invalidate_snapshot(m);
@@ -1253,5 +1300,6 @@ extern "C" ash_status ash_erase_noalloc(ash_map* m, const int32_t* keys, int64_t
   m->K.erase_mark(m->S, tv, keys, n, scratch, L);
   ash::launch_erase_resolve(m->S, tv, n, scratch, masks, L);
   m->heap_identity = false;
+  m->erased_since_snap += n;  // the map's next snapshot counts this call's tombstones
   return check_launch("erase_noalloc");
 }

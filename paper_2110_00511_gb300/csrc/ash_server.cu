@@ -144,6 +144,67 @@ class PinnedPool {
   std::map<int64_t, std::vector<void*>> spill_;     // cudaMallocHost blocks by size
 };
 
+// Device staging carved from one allocation made when the server is created
+// (staging_bytes, the admission budget), first-fit in 256-byte units with
+// coalescing frees: serving then calls no allocator per request.  A request
+// that does not fit (one larger than the budget is admitted alone, or the
+// free space is fragmented) gets a stream-ordered allocation instead.  Only
+// the worker thread uses it.
+class DeviceArena {
+ public:
+  void reserve(int64_t bytes) {
+    bytes = (bytes + kUnit - 1) / kUnit * kUnit;
+    if (bytes <= 0) return;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    base_ = static_cast<char*>(p);
+    size_ = bytes;
+    free_.emplace(0, bytes);
+  }
+  // nullptr when no free block is large enough
+  char* take(int64_t bytes, int64_t* taken) {
+    const int64_t need = (bytes + kUnit - 1) / kUnit * kUnit;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < need) continue;
+      const int64_t off = it->first, len = it->second;
+      free_.erase(it);
+      if (len > need) free_.emplace(off + need, len - need);
+      *taken = need;
+      return base_ + off;
+    }
+    return nullptr;
+  }
+  void give(char* p, int64_t taken) {
+    int64_t off = p - base_, len = taken;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + len == next->first) {
+      len += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        off = prev->first;
+        len += prev->second;
+        free_.erase(prev);
+      }
+    }
+    free_.emplace(off, len);
+  }
+  ~DeviceArena() {
+    if (base_) cudaFree(base_);
+  }
+
+ private:
+  static constexpr int64_t kUnit = 256;
+  char* base_ = nullptr;
+  int64_t size_ = 0;
+  std::map<int64_t, int64_t> free_;  // offset -> length
+};
+
 // Page-locked (pinned or registered) host memory, which copy engines read
 // directly.
 bool is_pinned(const void* p) {
@@ -173,6 +234,7 @@ struct Request {
   void* host = nullptr;
   int64_t host_cls = 0;
   char* dev = nullptr;
+  int64_t dev_taken = 0;     // bytes carved from the device arena; 0: a stream-ordered allocation
   Clock::time_point t_submit, t_done;
   bool gpu_done = false;
   bool delivered = false;
@@ -184,7 +246,7 @@ struct Request {
 // free them at any time; only the callback touches `reqs`, before that point.
 struct Batch {
   std::vector<Request*> reqs;
-  std::vector<char*> dev;
+  std::vector<std::pair<char*, int64_t>> dev;  // device staging and its arena bytes (0: allocated)
   int64_t staged = 0;
   struct ash_server* server = nullptr;
   bool done = false;
@@ -205,6 +267,7 @@ struct ash_server {
   std::vector<cudaEvent_t> grow_done;
   std::vector<char> growing;
   PinnedPool pinned;
+  DeviceArena arena;
   int64_t value_bytes = 0;
 
   std::mutex mu;
@@ -258,8 +321,9 @@ ash_status grow_for_insert(ash_server* s, int t, int64_t n) {
   // a table whose live + erased slots could pass max_used_fraction is rebuilt
   // here too (at the same capacity when the live entries still fit), so the
   // batch's own growth check never has to synchronise the compute stream
+  if (!(m->used_ub + n > max_used)) tighten_bounds(m);  // a landed snapshot may report new tombstones
   const bool grow = need > lim * static_cast<double>(m->capacity);
-  const bool rebuild = m->used_ub + n > max_used;
+  const bool rebuild = m->used_ub + n > max_used || tombstones_need_rebuild(m);
   if (!grow && !rebuild) return ASH_OK;
   // the new capacity holds the live entries and this insert under both
   // limits, so a rebuild is never followed by another one for the same batch
@@ -351,7 +415,10 @@ void worker_loop(ash_server* s) {
     }
     lk.unlock();
     for (Batch* b : finished) {
-      for (char* p : b->dev) cudaFreeAsync(p, s->s_d2h);
+      for (auto& d : b->dev) {
+        if (d.second > 0) s->arena.give(d.first, d.second);  // the batch is done: the block is free at once
+        else cudaFreeAsync(d.first, s->s_d2h);
+      }
       delete b;
     }
     finished.clear();
@@ -402,10 +469,15 @@ void worker_loop(ash_server* s) {
           ops.push_back(o);
           continue;
         }
-        if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, s->s_h2d) != cudaSuccess) {
-          cudaGetLastError();
-          st = ASH_ERR_OOM;
-          break;
+        r->dev = s->arena.take(r->bytes, &r->dev_taken);
+        if (!r->dev) {
+          r->dev_taken = 0;
+          if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, s->s_h2d) != cudaSuccess) {
+            cudaGetLastError();
+            r->dev = nullptr;
+            st = ASH_ERR_OOM;
+            break;
+          }
         }
         if (r->direct_in) {
           const int64_t kb = r->n * s->cfg.key_dim * 4;
@@ -457,7 +529,7 @@ void worker_loop(ash_server* s) {
         Batch* b = new Batch();
         b->reqs = pick;
         for (Request* r : pick) {
-          if (r->dev) b->dev.push_back(r->dev);
+          if (r->dev) b->dev.emplace_back(r->dev, r->dev_taken);
           b->staged += r->bytes;
         }
         b->server = s;
@@ -476,8 +548,10 @@ void worker_loop(ash_server* s) {
       }
     }
     if (st != ASH_OK) {
+      if (cudaStreamSynchronize(s->s_h2d) != cudaSuccess) cudaGetLastError();  // uploads issued for the failed batch
       for (Request* r : pick) {
-        if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
+        if (r->dev && r->dev_taken > 0) s->arena.give(r->dev, r->dev_taken);
+        else if (r->dev) cudaFreeAsync(r->dev, s->s_h2d);
         r->dev = nullptr;
       }
     }
@@ -536,6 +610,7 @@ ash_status ash_server_create(const ash_server_config* cfg, ash_server** out_host
   s->value_bytes = cfg->value_row_bytes;
   if (cfg->zero_copy != 1) s->pinned.reserve(cfg->staging_bytes);  // host staging as large as the device budget
   DeviceGuard g(cfg->device);
+  if (cfg->zero_copy != 1) s->arena.reserve(cfg->staging_bytes);     // device staging: the admission budget
   if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking) != cudaSuccess ||

@@ -767,3 +767,39 @@ def test_point_input_ops(d, cell):
     assert_op_parity(hs, keys, ai, am, aoi, aom)
     assert_same_map(hs, os_)
 
+
+
+def test_erase_churn_keeps_tombstones_bounded():
+    """Insert/erase churn on a table larger than the tombstone floor: erased
+    slots in full buckets stay tombstones, and the map rebuilds its table
+    (same capacity, same indices) once the known tombstones pass a quarter of
+    its live entries, so they never pile up; the map still equals the oracle
+    and its stats add up (live = size, used >= live)."""
+    rng = np.random.default_rng(77)
+    pool = np.unique(rng.integers(-(1 << 12), 1 << 12, size=(400_000, 3)).astype(np.int32), axis=0)
+    cap = 1 << 18
+    hm = ash.HashMap(3, cap, [(1,)], [torch.float32])
+    om = oracle.OracleMap(3, cap, [4])
+    worst = 0.0
+    for r in range(40):
+        a = int(rng.integers(0, len(pool) - 60_000))
+        ins = pool[a:a + 60_000]
+        vals = rng.random(len(ins), dtype=np.float32)
+        gi, gm = hm.insert(dev(ins), [dev(vals)])
+        oi, omask = om.insert(ins, [vals])
+        assert_op_parity(hm, ins, gi, gm, oi, omask)
+        b = int(rng.integers(0, len(pool) - 50_000))
+        er = pool[b:b + 50_000]
+        assert np.array_equal(hm.erase(dev(er)).cpu().numpy(), om.erase(er))
+        st = hm.stats()
+        assert st["live"] == om.size() and st["used_slots"] >= st["live"]
+        assert st["capacity"] == om.capacity() and st["table_slots"] >= 2 * st["capacity"]
+        if r >= 2:
+            worst = max(worst, (st["used_slots"] - st["live"]) / max(1, st["live"]))
+    st = hm.stats()
+    assert st["rebuilds"] > 0, st
+    # the bound acts on landed snapshots, so allow the tombstones of a few
+    # batches on top of a quarter of the live entries
+    assert worst < 1.0, worst
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
