@@ -1147,14 +1147,23 @@ def probe_random_gbs(buf_bytes, device, reps=3):
 
 
 def small_call_figures(keys, queries, n, device, flush, calls=64):
-    """Per-call cost of small batches, three ways (microseconds):
-      python:    CUDA events around one HashMap call (host time of the
-                 binding and the library included, as the sweep times it);
-      abi:       events around one call of the C ABI with outputs allocated
-                 beforehand (the library's host time and its kernels);
-      pipelined: `calls` calls issued back to back through HashMap (activate
-                 on as many fresh maps, find on one map), total time / calls:
-                 the cost per call when the host keeps the stream busy."""
+    """Per-call cost of small batches (microseconds), L2 flushed before each
+    single call:
+      python:        CUDA events around one HashMap call (host time of the
+                     binding and the library included, as the sweep times it);
+      abi:           events around one call of the C ABI with outputs
+                     allocated beforehand (the library's host time and its
+                     kernels);
+      gpu:           the same C ABI call queued behind a GPU sleep, so that
+                     the host's work is hidden: the device time of the call;
+      pipelined:     `calls` calls issued back to back through HashMap
+                     (activate on as many fresh maps, find on one map), total
+                     time / calls: the cost per call when the host keeps the
+                     stream busy;
+      abi_pipelined: the same through the C ABI.
+    floor_us: the python and gpu timings of one PyTorch call that launches a
+    single tiny kernel (a 16-element fill): what any one-kernel call costs in
+    this harness."""
     import torch
     from paper_2110_00511_gb300 import ash
     L = ash.lib()
@@ -1162,11 +1171,13 @@ def small_call_figures(keys, queries, n, device, flush, calls=64):
     msk = torch.empty(n, dtype=torch.bool, device=device)
     st = ash._stream_of(device.index)
 
-    def ev_span(fn, reps=5):
+    def ev_span(fn, reps=5, hide_host=False):
         best = None
         for _ in range(reps):
             flush.zero_()
             torch.cuda.synchronize()
+            if hide_host:
+                torch.cuda._sleep(2_000_000)  # about 1 ms: the call is queued before the GPU reaches it
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             fn()
@@ -1175,7 +1186,20 @@ def small_call_figures(keys, queries, n, device, flush, calls=64):
             best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
         return 1000.0 * best
 
+    def back_to_back(fns):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for fn in fns:
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return 1000.0 * e0.elapsed_time(e1) / len(fns)
+
     out = {}
+    tiny = torch.empty(16, dtype=torch.int32, device=device)
+    out["floor_us"] = {"python_one_kernel": ev_span(lambda: tiny.zero_()),
+                       "gpu_one_kernel": ev_span(lambda: tiny.zero_(), hide_host=True)}
     fresh = []
 
     def fresh_map():
@@ -1183,40 +1207,33 @@ def small_call_figures(keys, queries, n, device, flush, calls=64):
         torch.cuda.synchronize()
         return fresh[-1]
 
+    def abi_activate(m):
+        return lambda: L.ash_activate(m.handle, keys.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st)
+
     res = {}
-    for name in ("python", "abi"):
+    for name in ("python", "abi", "gpu"):
         best = None
         for _ in range(5):
             m = fresh_map()
             if name == "python":
                 us = ev_span(lambda: m.activate(keys), reps=1)
             else:
-                us = ev_span(lambda: L.ash_activate(m.handle, keys.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st),
-                             reps=1)
+                us = ev_span(abi_activate(m), reps=1, hide_host=name == "gpu")
             best = us if best is None else min(best, us)
         res[name] = best
     maps = [ash.HashMap(3, n, device=device) for _ in range(calls)]
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for m in maps:
-        m.activate(keys)
-    e1.record()
-    torch.cuda.synchronize()
-    res["pipelined"] = 1000.0 * e0.elapsed_time(e1) / calls
+    res["pipelined"] = back_to_back([(lambda m=m: m.activate(keys)) for m in maps])
+    maps2 = [ash.HashMap(3, n, device=device) for _ in range(calls)]
+    res["abi_pipelined"] = back_to_back([abi_activate(m) for m in maps2])
     out["activate_us"] = res
     m = maps[0]
-    res = {"python": ev_span(lambda: m.find(queries)),
-           "abi": ev_span(lambda: L.ash_find(m.handle, queries.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st))}
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(calls):
-        m.find(queries)
-    e1.record()
-    torch.cuda.synchronize()
-    res["pipelined"] = 1000.0 * e0.elapsed_time(e1) / calls
+    abi_find = lambda: L.ash_find(m.handle, queries.data_ptr(), n, idx.data_ptr(), msk.data_ptr(), st)
+    res = {"python": ev_span(lambda: m.find(queries)), "abi": ev_span(abi_find),
+           "gpu": ev_span(abi_find, hide_host=True),
+           "pipelined": back_to_back([lambda: m.find(queries)] * calls),
+           "abi_pipelined": back_to_back([abi_find] * calls)}
     out["find_us"] = res
-    del maps, fresh
+    del maps, maps2, fresh
     return out
 
 

@@ -36,7 +36,7 @@ __global__ void mark_free_kernel(const int32_t* __restrict__ heap, int64_t capac
                                  uint32_t* __restrict__ words) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctrl->count = 0;
-    ctrl->pad1 = 0;  // blocks of the compaction that have finished
+    ctrl->list_done = 0;
   }
   const int64_t t = static_cast<int64_t>(static_cast<uint32_t>(ctrl->top_used));
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kListThreads) compact_live_kernel(uint32_t* __
   }
   if (count_out != nullptr && threadIdx.x == 0) {
     __threadfence();
-    const unsigned long long done = atomicAdd(&ctrl->pad1, 1ull);
+    const unsigned long long done = atomicAdd(&ctrl->list_done, 1ull);
     if (done == gridDim.x - 1) {
       __threadfence();
       *count_out = static_cast<long long>(atomicAdd(&ctrl->count, 0ull));
@@ -166,6 +166,15 @@ __global__ void set_used_from_count_kernel(Ctrl* ctrl) {
 void launch_set_used_from_count(Ctrl* ctrl, const Launch& L) {
   TraceScope ts(kKSetCtrl, L.stream);
   set_used_from_count_kernel<<<1, 1, 0, L.stream>>>(ctrl);
+}
+
+__global__ void snapshot_kernel(Ctrl* ctrl, Snap* snap, uint32_t seq) {
+  if (threadIdx.x == 0) publish_snapshot(ctrl, snap, seq);
+}
+
+void launch_snapshot(Ctrl* ctrl, Snap* snap, uint32_t seq, const Launch& L) {
+  TraceScope ts(kKSetCtrl, L.stream);
+  snapshot_kernel<<<1, 32, 0, L.stream>>>(ctrl, snap, seq);
 }
 
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L) {

@@ -22,6 +22,8 @@ void launch_list_active(bool heap_identity, const int32_t* heap, int64_t capacit
                         int32_t* out, int64_t out_cap, long long* count_out, const Launch& L);
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L);
 void launch_set_used_from_count(Ctrl* ctrl, const Launch& L);
+// Publishes the control block to a host-visible snapshot (publish_snapshot).
+void launch_snapshot(Ctrl* ctrl, Snap* snap, uint32_t seq, const Launch& L);
 void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);
 void launch_scatter_rows(const ValueCopy& vc, const int32_t* idx, const uint8_t* mask, int64_t n, const Launch& L);
 void launch_gather_rows(const ValueCopy& vc, const int32_t* list, int64_t n, const Launch& L);

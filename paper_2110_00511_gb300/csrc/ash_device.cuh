@@ -52,9 +52,23 @@ struct Ctrl {
   // (committed + tombstones).  One 64-bit atomic updates both.
   unsigned long long top_used;
   int status;
-  int pad0;
+  unsigned int commit_done;   // blocks of a snapshotting commit that have finished
   unsigned long long count;   // listing counter
-  unsigned long long pad1;
+  unsigned long long list_done;  // blocks of a counting compaction that have finished
+};
+
+// Host-visible copy of a control block's counters, in mapped pinned memory:
+// the device writes it after a batch (the last block of the insert's commit,
+// or snapshot_kernel) so that the host can tighten its bounds on the live and
+// used counts without synchronising.  One 16-byte store writes top_used and
+// check = top_used ^ snap_tag(seq), seq being the number the host gave the
+// write; the host takes the record once the two words agree for that number
+// (a record not yet written, or half of a write, does not pass).  One 64-byte
+// line per map.
+struct Snap {
+  unsigned long long top_used;
+  unsigned long long check;
+  unsigned long long pad[6];
 };
 
 // View of one map handed to kernels by value.
@@ -73,6 +87,10 @@ struct TableView {
   // claim kernel a position holding a slot index wins unless its bit is set,
   // and the commit decides without reading the slot word.
   uint32_t* lost;
+  // Where the insert's commit publishes the control block when it finishes
+  // (null: no snapshot), and the sequence number of that write.
+  Snap* snap;
+  uint32_t snap_seq;
 };
 
 // TableView::flags: the free part of the heap is the identity (h[j] = j for
@@ -112,13 +130,26 @@ struct KeyStride {
 // constant, summed, then the splitmix64 finaliser (Steele et al. 2014) for
 // avalanche.  The home bucket uses the high 32 bits (multiply-shift range
 // reduction), the fingerprint the low 32 bits with the top bit forced on.
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
   x *= 0xBF58476D1CE4E5B9ull;
   x ^= x >> 27;
   x *= 0x94D049BB133111EBull;
   x ^= x >> 31;
   return x;
+}
+
+// Check word of snapshot number seq (a bijection of seq, never 0).
+__host__ __device__ __forceinline__ uint64_t snap_tag(uint32_t seq) {
+  return mix64(static_cast<uint64_t>(seq) + 0x9E3779B97F4A7C15ull);
+}
+
+// Copies the control block's counters to a host-visible snapshot: top_used
+// is read at L2 (the atomics of this kernel and earlier ones are all there),
+// then one 16-byte store writes it with its check word.
+__device__ __forceinline__ void publish_snapshot(Ctrl* ctrl, Snap* snap, uint32_t seq) {
+  const unsigned long long tu = atomicAdd(&ctrl->top_used, 0ull);
+  *reinterpret_cast<ulonglong2*>(snap) = make_ulonglong2(tu, tu ^ snap_tag(seq));
 }
 
 __device__ __forceinline__ uint64_t coord_mult(int j) {

@@ -50,11 +50,13 @@ struct ash_map {
   int64_t list_scratch_bytes = 0;
   int64_t size_ub = 0;  // upper bound of live entries since the last sync
   int64_t used_ub = 0;  // upper bound of used slots since the last sync
-  // Non-blocking snapshot of the control block: copied to snap_host after a
-  // batch (once the bounds pass half the limits), read when snap_event has
-  // completed, to tighten the bounds without synchronising.
-  ash::Ctrl* snap_host = nullptr;
-  cudaEvent_t snap_event = nullptr;
+  // Non-blocking snapshot of the control block: written by the device to
+  // snap_host (mapped pinned memory, snap_dev on the device) after a batch
+  // once the bounds pass half the limits, and read once its sequence number
+  // shows snap_seq, to tighten the bounds without synchronising.
+  ash::Snap* snap_host = nullptr;
+  ash::Snap* snap_dev = nullptr;
+  uint32_t snap_seq = 0;           // number of the last snapshot requested
   int snap_state = 0;              // 0 idle, 1 in flight, 2 in flight but stale
   int64_t added_since_snap = 0;    // insert/activate keys issued after the snapshot's copy
   // Lower bound on tombstones (used - live of the last landed snapshot):
@@ -122,7 +124,14 @@ ash_status grow_async(ash_map* m, int64_t new_capacity, cudaStream_t st);
 void tighten_bounds(ash_map* m);
 // Marks an in-flight snapshot stale (after clear / rebuild change the count).
 void invalidate_snapshot(ash_map* m);
-// Enqueues a control-block snapshot on st once a bound passes half its limit.
+// Whether to snapshot the control block after the batch being issued on st
+// (`added` insert keys not yet on the bounds): once a bound passes half its
+// limit, or after erases on a table of some size.  True takes the next
+// sequence number (m->snap_seq); the caller has the device publish it and
+// then calls snapshot_issued.
+bool snapshot_wanted(ash_map* m, cudaStream_t st, int64_t added);
+void snapshot_issued(ash_map* m);
+// snapshot_wanted(m, st, 0), published by snapshot_kernel.
 void maybe_snapshot(ash_map* m, cudaStream_t st);
 // Records the stream of an insert/activate (snapshots need a single one).
 void note_insert_stream(ash_map* m, cudaStream_t st);

@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(256) offsets_kernel(TableView t, const int32_t
 template <int D, int S, int KPT, class In = const int32_t*>
 __global__ void __launch_bounds__(256) find_kernel(TableView t, const In keys, int64_t n,
                                                    int32_t* __restrict__ idx, uint8_t* __restrict__ mask) {
+  // a programmatic dependent of the previous kernel: wait for its grid (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int KS = KeyStride<D>::value;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT + threadIdx.x; base < n; base += step) {
@@ -525,6 +527,8 @@ __device__ __forceinline__ void claim_from_bucket(const TableView& t, const In& 
 template <int D, int S, int KPT, class In = const int32_t*>
 __global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In keys, int64_t n,
                                                            int32_t* __restrict__ slot_out) {
+  // a programmatic dependent of the previous kernel: wait for its grid (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT + threadIdx.x; base < n; base += step) {
     int64_t p[KPT];
@@ -553,6 +557,8 @@ __global__ void __launch_bounds__(256) claim_bucket_kernel(TableView t, const In
 template <int D, int S, int KPT, class In = const int32_t*>
 __global__ void __launch_bounds__(256) claim_pref_kernel(TableView t, const In keys, int64_t n,
                                                          int32_t* __restrict__ slot_out) {
+  // a programmatic dependent of the previous kernel: wait for its grid (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int KS = KeyStride<D>::value;
   constexpr int kDL = KPT == 1 ? 1 : 2;      // queued keys per lane in a dense round
   constexpr int kDrain = 32 * kDL;
@@ -799,9 +805,21 @@ __global__ void __launch_bounds__(256) commit_kernel(TableView t, const In keys,
   __shared__ int s_warp[33];
   __shared__ int s_base;
   __shared__ int s_got;
+  // a programmatic dependent of the previous kernel: wait for its grid (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * KPT;
   for (int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * KPT; base0 < n; base0 += step)
     commit_tile<D, KPT, VAL, In, FLAGS>(t, keys, n, base0, idx, mask, v, s_warp, &s_base, &s_got);
+  // The last block to finish publishes the control block for the host's
+  // growth checks (every block's heap atomics were made by its thread 0).
+  if (t.snap != nullptr && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&t.ctrl->commit_done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      t.ctrl->commit_done = 0u;
+      publish_snapshot(t.ctrl, t.snap, t.snap_seq);
+    }
+  }
 }
 
 // --------------------------------------------------------------- erase: mark
@@ -974,6 +992,25 @@ struct Launch {
   int sms = 0;   // SM count (0: unknown)
 };
 
+// Launch with programmatic stream serialisation: the kernel's blocks may be
+// scheduled while the previous kernel on the stream drains, hiding the
+// launch latency between the two.  The kernel must execute
+// griddepcontrol.wait before it touches memory the previous kernel writes.
+template <class... P, class... A>
+inline void launch_dependent(void (*kernel)(P...), int grid, int block, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(block));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // Blocks of `kernel` (block threads `block`, no dynamic shared memory) that
 // fit on one SM, from the occupancy API, cached per kernel and block size.
 template <class K>
@@ -1031,7 +1068,8 @@ struct DimLaunchers {
   template <int S, int KPT, class In>
   static void find_sk(const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask, const Launch& L) {
     TraceScope ts(kKFind, L.stream);
-    find_kernel<D, S, KPT, In><<<grid_for((n + KPT - 1) / KPT, L), L.block, 0, L.stream>>>(t, keys, n, idx, mask);
+    launch_dependent(find_kernel<D, S, KPT, In>, grid_for((n + KPT - 1) / KPT, L), L.block, L.stream, t, keys, n, idx,
+                     mask);
   }
   template <int S, class In>
   static void find_s(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,
@@ -1066,11 +1104,11 @@ struct DimLaunchers {
     const int g = grid_for((n + KPT - 1) / KPT, L);
     if (pref) {
       auto* k = claim_pref_kernel<D, S, 1, In>;
-      k<<<resident_grid(k, grid_for(n, L), L), L.block, 0, L.stream>>>(t, keys, n, slot_out);
+      launch_dependent(k, resident_grid(k, grid_for(n, L), L), L.block, L.stream, t, keys, n, slot_out);
     } else {
       // (capping this grid at its 4 resident blocks per SM measured 10-15 %
       // slower on 1e7-key tables)
-      claim_bucket_kernel<D, S, KPT, In><<<g, L.block, 0, L.stream>>>(t, keys, n, slot_out);
+      launch_dependent(claim_bucket_kernel<D, S, KPT, In>, g, L.block, L.stream, t, keys, n, slot_out);
     }
   }
   template <int S, class In>
@@ -1100,8 +1138,8 @@ struct DimLaunchers {
                         const ValueRow& v, const Launch& L) {
     TraceScope ts(kKCommit, L.stream);
     const int g = grid_for((n + KPT - 1) / KPT, L);
-    if (t.lost) commit_kernel<D, KPT, VAL, In, true><<<g, L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
-    else commit_kernel<D, KPT, VAL, In, false><<<g, L.block, 0, L.stream>>>(t, keys, n, idx, mask, v);
+    if (t.lost) launch_dependent(commit_kernel<D, KPT, VAL, In, true>, g, L.block, L.stream, t, keys, n, idx, mask, v);
+    else launch_dependent(commit_kernel<D, KPT, VAL, In, false>, g, L.block, L.stream, t, keys, n, idx, mask, v);
   }
   template <bool VAL, class In>
   static void commit_v(int kpt, const TableView& t, const In& keys, int64_t n, int32_t* idx, uint8_t* mask,

@@ -75,6 +75,70 @@ void pinned_ctrl_give(ash::Ctrl* c) {
   g_pin_free.push_back(c);
 }
 
+// Snapshot records: mapped pinned memory that kernels write.  seq is the
+// last number given to the record.  A record given back while its last
+// snapshot may still land waits in g_snap_wait until that write shows.
+struct SnapRec {
+  ash::Snap* host;
+  ash::Snap* dev;
+  uint32_t seq;
+};
+std::vector<SnapRec> g_snap_free;
+std::vector<SnapRec> g_snap_wait;
+
+// The record's top_used if snapshot number seq has landed in it.
+bool snap_read(const ash::Snap* s, uint32_t seq, unsigned long long* top_used) {
+  const unsigned long long tu = __atomic_load_n(&s->top_used, __ATOMIC_ACQUIRE);
+  const unsigned long long check = __atomic_load_n(&s->check, __ATOMIC_ACQUIRE);
+  if ((tu ^ check) != ash::snap_tag(seq)) return false;
+  *top_used = tu;
+  return true;
+}
+
+bool snap_take(SnapRec* out) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  for (size_t i = 0; i < g_snap_wait.size();) {
+    unsigned long long tu;
+    if (snap_read(g_snap_wait[i].host, g_snap_wait[i].seq, &tu)) {
+      g_snap_free.push_back(g_snap_wait[i]);
+      g_snap_wait[i] = g_snap_wait.back();
+      g_snap_wait.pop_back();
+    } else {
+      ++i;
+    }
+  }
+  if (g_snap_free.empty()) {
+    constexpr int kPerPage = 128;
+    void* page = nullptr;
+    void* dpage = nullptr;
+    if (cudaHostAlloc(&page, sizeof(ash::Snap) * kPerPage, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaHostGetDevicePointer(&dpage, page, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(page);
+      return false;
+    }
+    std::memset(page, 0, sizeof(ash::Snap) * kPerPage);
+    for (int i = kPerPage - 1; i >= 0; --i)
+      g_snap_free.push_back({static_cast<ash::Snap*>(page) + i, static_cast<ash::Snap*>(dpage) + i, 0u});
+  }
+  *out = g_snap_free.back();
+  g_snap_free.pop_back();
+  return true;
+}
+
+// pending: snapshot number r.seq was requested and may not have landed.
+void snap_give(const SnapRec& r, bool pending) {
+  if (!r.host) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  unsigned long long tu;
+  if (pending && !snap_read(r.host, r.seq, &tu)) g_snap_wait.push_back(r);
+  else g_snap_free.push_back(r);
+}
+
 int64_t dtype_bytes(int32_t dt) {
   switch (dt) {
     case ASH_F32: case ASH_I32: return 4;
@@ -196,6 +260,8 @@ ash::TableView view_of(const ash_map* m) {
   t.capacity = static_cast<int32_t>(m->capacity);
   t.flags = (m->heap_identity ? ash::kViewHeapIdentity : 0) | (m->pref_placed ? ash::kViewPrefPlaced : 0);
   t.lost = nullptr;
+  t.snap = nullptr;
+  t.snap_seq = 0;
   return t;
 }
 
@@ -243,7 +309,7 @@ ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int
   if (status) *status = m->ctrl_host->status;
   m->size_ub = *top;
   m->used_ub = *used;
-  tighten_bounds(m);  // the stream is idle: a pending snapshot has landed
+  tighten_bounds(m);  // folds in a snapshot that has landed
   m->size_ub = *top;
   m->used_ub = *used;
   if (*used - *top > m->tomb_lb) m->tomb_lb = *used - *top;  // exact now
@@ -251,12 +317,9 @@ ash_status refresh(ash_map* m, cudaStream_t st, int64_t* top, int64_t* used, int
 }
 
 void tighten_bounds(ash_map* m) {
-  if (m->snap_state == 0 || cudaEventQuery(m->snap_event) != cudaSuccess) {
-    cudaGetLastError();  // cudaErrorNotReady is not an error here
-    return;
-  }
+  unsigned long long tu = 0;
+  if (m->snap_state == 0 || !snap_read(m->snap_host, m->snap_seq, &tu)) return;
   if (m->snap_state == 1) {
-    const unsigned long long tu = m->snap_host->top_used;
     const int64_t snap_top = static_cast<int64_t>(tu & 0xFFFFFFFFull);
     const int64_t snap_used = static_cast<int64_t>(tu >> 32);
     const int64_t top = snap_top + m->added_since_snap;
@@ -284,49 +347,47 @@ void invalidate_snapshot(ash_map* m) {
   if (m->snap_state == 1) m->snap_state = 2;
 }
 
-// After a batch: once a bound passes half its limit, copy the control block
-// to the snapshot mirror (asynchronously) so that a later growth check can
-// tighten the bound without a synchronisation.
 void note_insert_stream(ash_map* m, cudaStream_t st) {
   if (m->any_insert && m->insert_stream != st) m->insert_streams_mixed = true;
   m->insert_stream = st;
   m->any_insert = true;
 }
 
-void maybe_snapshot(ash_map* m, cudaStream_t st) {
+// Snapshots are taken once a bound passes half its limit, so that a later
+// growth check can tighten it without a synchronisation, and after erases on
+// a table of some size (the tombstone count).  One is in flight at a time.
+bool snapshot_wanted(ash_map* m, cudaStream_t st, int64_t added) {
   // a snapshot that has landed is folded into the bounds first, so a fresh
   // one can be taken: the bounds then lag the device by the batches issued
   // since the last snapshot landed, not since the first one was taken
   if (m->snap_state != 0) tighten_bounds(m);
-  if (m->snap_state != 0 || !m->snap_host || m->insert_streams_mixed || st != m->insert_stream) return;
+  if (m->snap_state != 0 || !m->snap_host || m->insert_streams_mixed || st != m->insert_stream) return false;
+  const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
+  const bool churn = m->erased_since_snap > 0 && m->n_slots >= (int64_t{1} << 16);
+  if (2 * (m->size_ub + added) <= m->capacity && 2 * (m->used_ub + added) <= max_used && !churn) return false;
   // Never inside a stream capture: a replayed graph would write the pinned
-  // slot long after this map (and its slot) are gone.
+  // record long after this map (and its record) are gone.
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
     cudaGetLastError();
-    return;
+    return false;
   }
-  if (cs != cudaStreamCaptureStatusNone) return;
-  const int64_t max_used = static_cast<int64_t>(m->tuning.max_used_fraction * static_cast<double>(m->n_slots));
-  // snapshots serve the growth check (once a bound passes half its limit)
-  // and the tombstone count (after erases on a table of some size)
-  const bool churn = m->erased_since_snap > 0 && m->n_slots >= (int64_t{1} << 16);
-  if (2 * m->size_ub <= m->capacity && 2 * m->used_ub <= max_used && !churn) return;
-  if (!m->snap_event) {
-    if (cudaEventCreateWithFlags(&m->snap_event, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      m->snap_event = nullptr;
-      return;
-    }
-  }
-  if (cudaMemcpyAsync(m->snap_host, m->ctrl, sizeof(ash::Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaEventRecord(m->snap_event, st) != cudaSuccess) {
-    cudaGetLastError();
-    return;
-  }
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  ++m->snap_seq;
+  return true;
+}
+
+// The snapshot numbered m->snap_seq follows every batch issued so far.
+void snapshot_issued(ash_map* m) {
   m->snap_state = 1;
   m->added_since_snap = 0;
   m->erased_since_snap = 0;
+}
+
+void maybe_snapshot(ash_map* m, cudaStream_t st) {
+  if (!snapshot_wanted(m, st, 0)) return;
+  ash::launch_snapshot(m->ctrl, m->snap_dev, m->snap_seq, launch_of(m, st));
+  snapshot_issued(m);
 }
 
 ash_status status_from_bits(int bits) {
@@ -696,6 +757,13 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
     }
   }
   tv.lost = m->win_bits;
+  // the commit's last block publishes the control block when a snapshot is due
+  note_insert_stream(m, st);
+  const bool snap = snapshot_wanted(m, st, n);
+  if (snap) {
+    tv.snap = m->snap_dev;
+    tv.snap_seq = m->snap_seq;
+  }
   if (pts) {
     m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
     m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
@@ -709,8 +777,7 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   m->size_ub += n;
   m->used_ub += n;
   m->added_since_snap += n;
-  note_insert_stream(m, st);
-  maybe_snapshot(m, st);
+  if (snap) snapshot_issued(m);
   return check_launch("insert");
 }
 
@@ -785,13 +852,15 @@ ash_status ash_create(int key_dim, int64_t capacity, int n_values, const int64_t
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
   m->ctrl_host = pinned_ctrl_take();
-  m->snap_host = pinned_ctrl_take();
-  if (!m->ctrl_host || !m->snap_host) {
+  SnapRec rec{nullptr, nullptr, 0u};
+  if (!m->ctrl_host || !snap_take(&rec)) {
     pinned_ctrl_give(m->ctrl_host);
-    pinned_ctrl_give(m->snap_host);
     delete m;
     return fail(ASH_ERR_OOM, "pinned host allocation failed");
   }
+  m->snap_host = rec.host;
+  m->snap_dev = rec.dev;
+  m->snap_seq = rec.seq;
   m->ctrl = static_cast<ash::Ctrl*>(dev_alloc(m, sizeof(ash::Ctrl), st));
   if (!m->ctrl) { ash_destroy(m); return fail(ASH_ERR_OOM, "device allocation failed"); }
   if (cudaMemsetAsync(m->ctrl, 0, sizeof(ash::Ctrl), st) != cudaSuccess) {
@@ -821,14 +890,8 @@ ash_status ash_destroy(ash_map* m) {
   dev_free(m, m->list_scratch, st);
   dev_free(m, m->ctrl, st);
   pinned_ctrl_give(m->ctrl_host);
-  if (m->snap_event) {
-    // a snapshot copy may still be landing in the pinned slot: let it finish
-    // before the slot goes back to the pool
-    if (m->snap_state != 0) cudaEventSynchronize(m->snap_event);
-    cudaEventDestroy(m->snap_event);
-    cudaGetLastError();
-  }
-  pinned_ctrl_give(m->snap_host);
+  // a snapshot still in flight keeps its record out of the pool until it lands
+  snap_give({m->snap_host, m->snap_dev, m->snap_seq}, m->snap_state != 0);
   delete m;
   return ASH_OK;
 }

@@ -736,6 +736,32 @@ def test_repeated_batches_near_capacity(two_streams):
     assert_heap_permutation(hm)
 
 
+def test_commit_snapshot_avoids_host_sync():
+    """The insert's commit publishes the control block when the bound on the
+    live count passes half the capacity (Sec. 4.5 growth check without a
+    synchronisation): 6000 keys with 3000 distinct ones, then 6000 keys with
+    3000 new distinct ones into capacity 10^4.  The loose bound (12000) would
+    force a synchronising read; the landed snapshot (3000 + 6000) does not.
+    Results equal the oracle's and the capacity stays."""
+    rng = np.random.default_rng(17)
+    pool = np.unique(rng.integers(-50_000, 50_000, size=(7_000, 3)).astype(np.int32), axis=0)[:6_000]
+    a, b = pool[:3_000], pool[3_000:]
+    hm = ash.HashMap(3, 10_000)
+    om = oracle.OracleMap(3, 10_000, [])
+    runs = []
+    for part in (a, b):
+        keys = np.concatenate([part, part[rng.permutation(len(part))]])
+        runs.append((keys, hm.activate(dev(keys))))
+        torch.cuda.synchronize()  # the snapshot has landed
+    st = hm.stats()  # its own read is the one synchronising read
+    assert st["host_syncs"] == 1, st
+    for keys, (gi, gm) in runs:
+        oi, omask = om.activate(keys)
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert hm.capacity() == om.capacity() == 10_000
+    assert_same_map(hm, om)
+
+
 @pytest.mark.parametrize("d,cell", [(3, 0.005), (3, 0.048), (2, 0.01), (1, 0.25)])
 def test_point_input_ops(d, cell):
     """insert / activate / find on float32 points quantised in the kernels
