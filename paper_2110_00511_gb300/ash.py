@@ -40,7 +40,7 @@ class Tuning(ctypes.Structure):
                 ("max_used_fraction", ctypes.c_float), ("inline_value_bytes", ctypes.c_int32),
                 ("keys_per_thread", ctypes.c_int32), ("warp_probe", ctypes.c_int32),
                 ("find_keys_per_thread", ctypes.c_int32), ("claim_mode", ctypes.c_int32),
-                ("commit_keys_per_thread", ctypes.c_int32)]
+                ("commit_keys_per_thread", ctypes.c_int32), ("partition_keys", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

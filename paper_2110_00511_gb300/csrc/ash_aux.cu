@@ -20,6 +20,74 @@ void launch_erase_resolve(int S, const TableView& t, int64_t n, const int32_t* s
   else erase_resolve_s<16>(t, n, slot_in, mask, L);
 }
 
+// ------------------------------------------------------- key partitioning
+// One block per range: its row of per-block counts (G <= a few thousand
+// words) becomes the row's exclusive scan, and the row total is kept.
+__global__ void __launch_bounds__(256) partition_scan_kernel(uint32_t* __restrict__ counts, int G,
+                                                             uint32_t* __restrict__ range_totals) {
+  __shared__ int s_warp[33];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  uint32_t* row = counts + static_cast<int64_t>(blockIdx.x) * G;
+  const int per = (G + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per;
+  const int hi = lo + per < G ? lo + per : G;
+  uint32_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += row[i];
+  int total;
+  uint32_t at = static_cast<uint32_t>(block_exclusive_scan(static_cast<int>(sum), total, s_warp));
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t c = row[i];
+    row[i] = at;
+    at += c;
+  }
+  if (threadIdx.x == 0) range_totals[blockIdx.x] = static_cast<uint32_t>(total);
+}
+
+void launch_partition_scan(uint32_t* counts, int G, int P, uint32_t* range_totals, const Launch& L) {
+  launch_dependent(partition_scan_kernel, P, 256, L.stream, counts, G, range_totals);
+}
+
+// Four positions per thread: the dest loads, then the gathers, then the
+// stores.  A gather follows one of P runs that each advance in order.
+__global__ void __launch_bounds__(256) unpermute_kernel(const int32_t* __restrict__ dest, int64_t n,
+                                                        const int32_t* __restrict__ idx_p,
+                                                        const uint8_t* __restrict__ mask_p, int32_t* __restrict__ idx,
+                                                        uint8_t* __restrict__ mask) {
+  constexpr int U = 4;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * U;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x * U + threadIdx.x; base < n; base += step) {
+    int32_t d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t pos = base + static_cast<int64_t>(u) * blockDim.x;
+      d[u] = pos < n ? dest[pos] : 0;
+    }
+    int32_t i[U];
+    uint8_t m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t pos = base + static_cast<int64_t>(u) * blockDim.x;
+      i[u] = pos < n ? idx_p[d[u]] : 0;
+      m[u] = pos < n ? mask_p[d[u]] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t pos = base + static_cast<int64_t>(u) * blockDim.x;
+      if (pos < n) {
+        idx[pos] = i[u];
+        mask[pos] = m[u];
+      }
+    }
+  }
+}
+
+void launch_unpermute(const int32_t* dest, int64_t n, const int32_t* idx_p, const uint8_t* mask_p, int32_t* idx,
+                      uint8_t* mask, const Launch& L) {
+  TraceScope ts(kKUnpermute, L.stream);
+  launch_dependent(unpermute_kernel, grid_for((n + 3) / 4, L), L.block, L.stream, dest, n, idx_p, mask_p, idx, mask);
+}
+
 // ----------------------------------------------------------- active listing
 // Live indices are the complement of the heap's free part h[t..c) (the heap
 // keeps active + free a permutation of 0..c-1).  Free indices are marked in a

@@ -822,6 +822,181 @@ __global__ void __launch_bounds__(256) commit_kernel(TableView t, const In keys,
   }
 }
 
+// ------------------------------------------------------- key partitioning
+// For tables larger than L2, a call's keys are first put in the order of
+// their home buckets' ranges: P = 2^log_p ranges of consecutive buckets (the
+// top log_p bits of the hash word the home bucket comes from), a stable
+// partition, so that equal keys keep their input order and the lowest
+// position still wins.  The claim, commit and find kernels walk their keys
+// in order, so each then works on one range of the table at a time, and of
+// kB too once the commit has handed out indices in the same order, and
+// finds it in L2.
+//
+// Each of G blocks owns a contiguous span of whole tiles of kPartTile input
+// keys.  A count pass histograms each block's span per range (counts[P][G]);
+// a scan turns each range's row into the blocks' offsets within the range
+// (and the range totals); the scatter pass sorts each tile by range in
+// shared memory (stable: warp w holds tile positions [256 w, 256 w + 256) in
+// steps of 32, ranked by __match_any_sync) and writes each range's part of
+// the tile as one run after the block's previous tiles' runs.  dest[pos]
+// records where input row pos went, for the outputs' way back.
+constexpr int kPartTile = 2048;     // keys per tile: 256 threads x 8
+constexpr int kPartSteps = kPartTile / 256;
+constexpr int kPartMaxLog = 8;      // at most 256 ranges
+constexpr uint32_t kNoRange = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t key_range(uint64_t h, int log_p) { return hi32(h) >> (32 - log_p); }
+
+// The kPartSteps key rows of one lane in warp w's part of a tile (local
+// positions 256 w + 32 j + lane) and their ranges (kNoRange past the tile).
+template <int D>
+__device__ __forceinline__ void load_tile_rows(const int32_t* __restrict__ keys, int64_t base, int tn, int log_p,
+                                               int32_t (&k)[kPartSteps][D], uint32_t (&r)[kPartSteps]) {
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kPartSteps; ++j) {
+    const int local = w * 256 + j * 32 + lane;
+    if (local < tn) {
+      load_input_key<D>(keys, base + local, k[j]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c) k[j][c] = 0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPartSteps; ++j)
+    r[j] = w * 256 + j * 32 + lane < tn ? key_range(hash_key<D>(k[j]), log_p) : kNoRange;
+}
+
+// counts[p * G + b]: keys of range p in block b's span.
+template <int D>
+__global__ void __launch_bounds__(256) partition_count_kernel(const int32_t* __restrict__ keys, int64_t n, int log_p,
+                                                              int tiles_per_block, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_hist[1 << kPartMaxLog];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int P = 1 << log_p;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) s_hist[p] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * tiles_per_block * kPartTile;
+  const int64_t t1 = t0 + static_cast<int64_t>(tiles_per_block) * kPartTile < n
+                         ? t0 + static_cast<int64_t>(tiles_per_block) * kPartTile
+                         : n;
+  for (int64_t base = t0; base < t1; base += kPartTile) {
+    const int tn = t1 - base < kPartTile ? static_cast<int>(t1 - base) : kPartTile;
+    int32_t k[kPartSteps][D];
+    uint32_t r[kPartSteps];
+    load_tile_rows<D>(keys, base, tn, log_p, k, r);
+#pragma unroll
+    for (int j = 0; j < kPartSteps; ++j) {
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, r[j]);
+      if (r[j] != kNoRange && lane == __ffs(peers) - 1) atomicAdd(&s_hist[r[j]], static_cast<uint32_t>(__popc(peers)));
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) counts[static_cast<int64_t>(p) * gridDim.x + blockIdx.x] = s_hist[p];
+}
+
+// Dynamic shared memory of the scatter kernel: the tile's key rows.
+template <int D>
+constexpr size_t partition_scatter_smem() {
+  return sizeof(int32_t) * kPartTile * D;
+}
+
+// row_offsets: counts after the scan (block b's first place within range p);
+// range_totals: keys per range.
+template <int D>
+__global__ void __launch_bounds__(256) partition_scatter_kernel(const int32_t* __restrict__ keys, int64_t n, int log_p,
+                                                                int tiles_per_block,
+                                                                const uint32_t* __restrict__ row_offsets,
+                                                                const uint32_t* __restrict__ range_totals,
+                                                                int32_t* __restrict__ keys_out,
+                                                                int32_t* __restrict__ dest) {
+  extern __shared__ int32_t s_keys[];  // [kPartTile][D], the tile in range order
+  __shared__ uint32_t s_run[1 << kPartMaxLog];    // next place of each range for this block
+  __shared__ uint32_t s_start[1 << kPartMaxLog];  // first tile slot of each range
+  __shared__ uint32_t s_tcnt[1 << kPartMaxLog];   // the tile's keys of each range
+  __shared__ uint32_t s_cnt[8][1 << kPartMaxLog]; // per warp: keys of each range, then its offset in the range
+  __shared__ uint16_t s_pos[kPartTile];           // tile position of each slot
+  __shared__ uint8_t s_r[kPartTile];              // range of each slot
+  __shared__ int s_warp[33];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int P = 1 << log_p;
+  const int tid = threadIdx.x;
+  const int w = tid >> 5;
+  const int lane = tid & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  {
+    int unused;
+    const uint32_t tot = tid < P ? range_totals[tid] : 0u;
+    const uint32_t start = static_cast<uint32_t>(block_exclusive_scan(static_cast<int>(tot), unused, s_warp));
+    if (tid < P) s_run[tid] = start + row_offsets[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x];
+    __syncthreads();
+  }
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * tiles_per_block * kPartTile;
+  const int64_t t1 = t0 + static_cast<int64_t>(tiles_per_block) * kPartTile < n
+                         ? t0 + static_cast<int64_t>(tiles_per_block) * kPartTile
+                         : n;
+  for (int64_t base = t0; base < t1; base += kPartTile) {
+    const int tn = t1 - base < kPartTile ? static_cast<int>(t1 - base) : kPartTile;
+    for (int p = lane; p < P; p += 32) s_cnt[w][p] = 0u;
+    __syncwarp();
+    int32_t k[kPartSteps][D];
+    uint32_t r[kPartSteps];
+    load_tile_rows<D>(keys, base, tn, log_p, k, r);
+    uint32_t rank[kPartSteps];
+#pragma unroll
+    for (int j = 0; j < kPartSteps; ++j) {
+      const bool valid = r[j] != kNoRange;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, r[j]);
+      const uint32_t c = valid ? s_cnt[w][r[j]] : 0u;
+      rank[j] = c + __popc(peers & lt);
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) s_cnt[w][r[j]] = c + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tc = 0;
+    if (tid < P) {
+      for (int ww = 0; ww < 8; ++ww) {
+        const uint32_t c = s_cnt[ww][tid];
+        s_cnt[ww][tid] = tc;
+        tc += c;
+      }
+    }
+    int tile_total;
+    const uint32_t st = static_cast<uint32_t>(block_exclusive_scan(static_cast<int>(tc), tile_total, s_warp));
+    if (tid < P) {
+      s_start[tid] = st;
+      s_tcnt[tid] = tc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPartSteps; ++j) {
+      if (r[j] != kNoRange) {
+        const uint32_t slot = s_start[r[j]] + s_cnt[w][r[j]] + rank[j];
+#pragma unroll
+        for (int c = 0; c < D; ++c) s_keys[slot * D + c] = k[j][c];
+        s_pos[slot] = static_cast<uint16_t>(w * 256 + j * 32 + lane);
+        s_r[slot] = static_cast<uint8_t>(r[j]);
+      }
+    }
+    __syncthreads();
+    for (int slot = tid; slot < tn; slot += blockDim.x) {
+      const uint32_t rr = s_r[slot];
+      const uint32_t d = s_run[rr] + (slot - s_start[rr]);
+      int32_t* row = keys_out + static_cast<int64_t>(d) * D;
+#pragma unroll
+      for (int c = 0; c < D; ++c) row[c] = s_keys[slot * D + c];
+      dest[base + s_pos[slot]] = static_cast<int32_t>(d);
+    }
+    __syncthreads();
+    if (tid < P) s_run[tid] += s_tcnt[tid];
+    __syncthreads();
+  }
+}
+
 // --------------------------------------------------------------- erase: mark
 // Finds input row pos and marks its slot with the lowest position seen
 // (atomicMin into the high word, the buffer index kept in the low word).
@@ -997,11 +1172,12 @@ struct Launch {
 // launch latency between the two.  The kernel must execute
 // griddepcontrol.wait before it touches memory the previous kernel writes.
 template <class... P, class... A>
-inline void launch_dependent(void (*kernel)(P...), int grid, int block, cudaStream_t st, A... args) {
+inline void launch_dependent_smem(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t st,
+                                  A... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(grid));
   cfg.blockDim = dim3(static_cast<unsigned>(block));
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1009,6 +1185,11 @@ inline void launch_dependent(void (*kernel)(P...), int grid, int block, cudaStre
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
+template <class... P, class... A>
+inline void launch_dependent(void (*kernel)(P...), int grid, int block, cudaStream_t st, A... args) {
+  launch_dependent_smem(kernel, grid, block, 0, st, args...);
 }
 
 // Blocks of `kernel` (block threads `block`, no dynamic shared memory) that
@@ -1042,6 +1223,34 @@ inline int grid_for(int64_t n, const Launch& L) {
   return g < 1 ? 1 : static_cast<int>(g);
 }
 
+// Defined in ash_aux.cu.  Per range (one block each): the row of per-block
+// counts counts[p][0..G) becomes its exclusive scan, the row's total goes to
+// range_totals[p].
+void launch_partition_scan(uint32_t* counts, int G, int P, uint32_t* range_totals, const Launch& L);
+// idx[pos] = idx_p[dest[pos]], mask[pos] = mask_p[dest[pos]]: a partitioned
+// call's outputs back in input order.
+void launch_unpermute(const int32_t* dest, int64_t n, const int32_t* idx_p, const uint8_t* mask_p, int32_t* idx,
+                      uint8_t* mask, const Launch& L);
+
+// Blocks of a partition pass over n keys (G) and whole tiles per block.
+inline int partition_grid(int64_t n, const Launch& L, int* tiles_per_block) {
+  const int64_t tiles = (n + kPartTile - 1) / kPartTile;
+  const int64_t cap = L.sms > 0 ? static_cast<int64_t>(L.sms) * 4 : 512;
+  const int64_t g0 = tiles < cap ? tiles : cap;
+  const int64_t tpb = (tiles + g0 - 1) / g0;
+  *tiles_per_block = static_cast<int>(tpb);
+  const int64_t g = (tiles + tpb - 1) / tpb;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
+
+// Count words of a partitioned call on n keys (counts[P][G] and the P range
+// totals).
+inline int64_t partition_count_words(int64_t n, int log_p, const Launch& L) {
+  int tpb = 0;
+  const int64_t G = partition_grid(n, L, &tpb);
+  return (G + 1) * (int64_t{1} << log_p);
+}
+
 // Function table for one key dimension (filled in by ash_dim.cu).  S: slots
 // per bucket (4, 8, 16); kpt: keys per thread (1, 2, 4).
 struct DimKernels {
@@ -1056,6 +1265,8 @@ struct DimKernels {
   void (*offsets)(int S, const TableView&, const int32_t*, int64_t, const int32_t*, int64_t, int32_t*, uint8_t*,
                   const Launch&);
   void (*find_group)(int S, const TableView&, const int32_t*, int64_t, int32_t*, uint8_t*, const Launch&);
+  // stable partition of n key rows by home-bucket range (scratch: see partition_bytes)
+  void (*partition)(const int32_t*, int64_t, int, uint32_t*, int32_t*, int32_t*, const Launch&);
   // the same operations on float32 points quantised in the kernels
   void (*find_pts)(int S, int kpt, const TableView&, const PointRows&, int64_t, int32_t*, uint8_t*, const Launch&);
   void (*claim_pts)(int S, int kpt, int pref, const TableView&, const PointRows&, int64_t, int32_t*, const Launch&);
@@ -1224,8 +1435,30 @@ struct DimLaunchers {
     else if (S == 8) find_group_s<8>(t, keys, n, idx, mask, L);
     else find_group_s<16>(t, keys, n, idx, mask, L);
   }
+  // counts: partition_count_words(n, log_p, L) words; keys_out: n rows; dest: n.
+  static void partition(const int32_t* keys, int64_t n, int log_p, uint32_t* counts, int32_t* keys_out, int32_t* dest,
+                        const Launch& L) {
+    TraceScope ts(kKPartition, L.stream, 3);
+    int tpb = 0;
+    const int G = partition_grid(n, L, &tpb);
+    const int P = 1 << log_p;
+    uint32_t* range_totals = counts + static_cast<int64_t>(P) * G;
+    launch_dependent(partition_count_kernel<D>, G, 256, L.stream, keys, n, log_p, tpb, counts);
+    launch_partition_scan(counts, G, P, range_totals, L);
+    constexpr size_t smem = partition_scatter_smem<D>();
+    static bool attr_set = false;  // per key dimension; above 48 KB the kernel must opt in
+    if (!attr_set) {
+      cudaFuncSetAttribute(partition_scatter_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+      attr_set = true;
+    }
+    launch_dependent_smem(partition_scatter_kernel<D>, G, 256, smem, L.stream, keys, n, log_p, tpb,
+                          static_cast<const uint32_t*>(counts), static_cast<const uint32_t*>(range_totals), keys_out,
+                          dest);
+  }
   static DimKernels table() {
     DimKernels k;
+    k.partition = &partition;
     k.neighbors = &neighbors;
     k.offsets = &offsets;
     k.find_group = &find_group;

@@ -232,10 +232,73 @@ ash::DimKernels kernels_for(int d) {
 // preferred-slot path is 6-25 % faster up to 80 MB tables, even at 96 MB and
 // 19 % slower at 128 MB.  It needs the preferred-slot invariant, which a
 // bucket-first or batched insert gives up until the next clear or rebuild.
+// The preferred-slot claim pays off while the table is in L2: its CAS has
+// no load before it, and a CAS that misses L2 waits on DRAM in the atomic
+// unit.  (Keys in home-bucket range order do not change this: a range's
+// lines are not in L2 when its keys arrive, and the bucket-first claim ran
+// 3.6 against 5.1 ms on 10^8 ranged keys.)
 int claim_prefers_slot(const ash_map* m) {
   if (m->tuning.claim_mode == 1 || !m->pref_placed) return 0;
   if (m->tuning.claim_mode == 2) return 1;
   return m->n_slots * 8 * 3 <= l2_bytes(m->device) * 2 ? 1 : 0;
+}
+
+// log2 of the number of home-bucket ranges a call on n keys is partitioned
+// into, 0 for input order (tuning.partition_keys): ranges of at most L2/4
+// bytes of table, 2 to 256 of them (8 at least when forced).  By default,
+// calls of 2^20 keys or more on a table larger than twice L2.  The pay-off
+// needs both sides: a ranged find reads kB in range order only if the
+// inserts handed out indices in range order too.  Measured on GB300
+// (uniform keys, uniqueness 0.5, capacity n, queries in a fresh random
+// order), ranged against input order: at 2x10^7 keys activate 1.19 / 1.21 ms
+// and find 0.57 / 0.81 ms; at 10^8 activate 7.5 / 8.0 ms and find 4.6 /
+// 5.2 ms; at 10^7 (table 1.2x L2) activate 0.54-0.59 / 0.53 ms.
+int partition_log(const ash_map* m, int64_t n) {
+  const int mode = m->tuning.partition_keys;
+  if (mode == 1 || n <= 0) return 0;
+  const int64_t table = m->n_slots * 8;
+  const int64_t l2 = l2_bytes(m->device);
+  if (mode == 0 && (table <= 2 * l2 || n < (int64_t{1} << 20))) return 0;
+  int lg = 1;
+  while (lg < ash::kPartMaxLog && (table >> lg) > l2 / 4) ++lg;
+  return mode == 2 ? std::max(lg, 3) : lg;
+}
+
+// Stream-ordered scratch of one partitioned call, freed on the same stream
+// after its last kernel (concurrent finds on one map each have their own).
+struct PartBufs {
+  void* mem = nullptr;
+  int32_t* keys = nullptr;  // key rows in range order
+  int32_t* dest = nullptr;  // place of input row pos in that order
+  int32_t* idx = nullptr;   // outputs in range order
+  uint8_t* mask = nullptr;
+};
+
+// False (nothing enqueued) when the scratch cannot be had: the call then
+// uses its keys in input order.
+bool partition_call(ash_map* m, const int32_t* keys, int64_t n, int log_p, cudaStream_t st, PartBufs* pb) {
+  auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+  const int64_t words = up(ash::partition_count_words(n, log_p, launch_of(m, st)) * 4);
+  const int64_t rows = up(n * m->key_dim * 4);
+  const int64_t ints = up(n * 4);
+  char* base = static_cast<char*>(dev_alloc(m, words + rows + 2 * ints + up(n), st));
+  if (!base) {
+    cudaGetLastError();
+    return false;
+  }
+  pb->mem = base;
+  pb->keys = reinterpret_cast<int32_t*>(base + words);
+  pb->dest = reinterpret_cast<int32_t*>(base + words + rows);
+  pb->idx = reinterpret_cast<int32_t*>(base + words + rows + ints);
+  pb->mask = reinterpret_cast<uint8_t*>(base + words + rows + 2 * ints);
+  m->K.partition(keys, n, log_p, reinterpret_cast<uint32_t*>(base), pb->keys, pb->dest, launch_of(m, st));
+  return true;
+}
+
+// The partitioned call's outputs back in input order; its scratch freed.
+void partition_finish(ash_map* m, const PartBufs& pb, int64_t n, int32_t* idx, uint8_t* mask, cudaStream_t st) {
+  ash::launch_unpermute(pb.dest, n, pb.idx, pb.mask, idx, mask, launch_of(m, st));
+  dev_free(m, pb.mem, st);
 }
 
 ash::Launch launch_of(const ash_map* m, cudaStream_t st) {
@@ -287,6 +350,7 @@ ash_status validate_tuning(const ash_tuning& t) {
   if (t.commit_keys_per_thread != 0 && t.commit_keys_per_thread != 1 && t.commit_keys_per_thread != 2 &&
       t.commit_keys_per_thread != 4)
     return fail(ASH_ERR_INVALID, "commit_keys_per_thread must be 0, 1, 2 or 4");
+  if (t.partition_keys < 0 || t.partition_keys > 2) return fail(ASH_ERR_INVALID, "partition_keys must be 0, 1 or 2");
   return ASH_OK;
 }
 
@@ -724,6 +788,15 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   if (s != ASH_OK) return s;
   s = ensure_win_bits(m, n, st);
   if (s != ASH_OK) return s;
+  // int32 keys and no value rows to copy: the keys may go in home-bucket
+  // range order (the claim and commit then see positions in that order, and
+  // equal keys keep their input order)
+  int log_p = (pts || (values_host && m->n_values > 0)) ? 0 : partition_log(m, n);
+  PartBufs pb;
+  if (log_p > 0 && !partition_call(m, keys, n, log_p, st, &pb)) log_p = 0;
+  const int32_t* ckeys = log_p > 0 ? pb.keys : keys;
+  int32_t* cidx = log_p > 0 ? pb.idx : idx;
+  uint8_t* cmask = log_p > 0 ? pb.mask : mask;
   // an insert that stopped between its claim and its commit left flags set
   if (!m->win_bits_clean) ASH_CUDA(cudaMemsetAsync(m->win_bits, 0, m->win_bits_bytes, st));
   m->win_bits_clean = false;  // until every commit of this insert is enqueued
@@ -768,9 +841,10 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
     m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
     m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
   } else {
-    m->K.claim(m->S, kpt, pref, tv, keys, n, idx, L);
-    m->K.commit(ckpt, tv, keys, n, idx, mask, inline_value ? &vr : nullptr, L);
+    m->K.claim(m->S, kpt, pref, tv, ckeys, n, cidx, L);
+    m->K.commit(ckpt, tv, ckeys, n, cidx, cmask, inline_value ? &vr : nullptr, L);
   }
+  if (log_p > 0) partition_finish(m, pb, n, idx, mask, st);
   if (vc.n > 0) ash::launch_scatter_rows(vc, idx, mask, n, L);
   if (!pref) m->pref_placed = false;  // the bucket-first claim places keys in slot order
   m->win_bits_clean = true;  // the commits clear every winner-flag word they read
@@ -803,6 +877,7 @@ void ash_default_tuning(ash_tuning* out) {
   out->find_keys_per_thread = 1;
   out->claim_mode = 0;
   out->commit_keys_per_thread = 1;
+  out->partition_keys = 0;
 }
 
 ash_status ash_set_allocator(ash_alloc_fn alloc_fn, ash_free_fn free_fn, void* ctx) {
@@ -916,11 +991,18 @@ ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_ind
   DeviceGuard g(m->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   m->last_stream = st;
+  int log_p = partition_log(m, n);
+  PartBufs pb;
+  if (log_p > 0 && !partition_call(m, keys, n, log_p, st, &pb)) log_p = 0;
+  const int32_t* fkeys = log_p > 0 ? pb.keys : keys;
+  int32_t* fidx = log_p > 0 ? pb.idx : buf_indices;
+  uint8_t* fmask = log_p > 0 ? pb.mask : masks;
   if (m->tuning.warp_probe == 1)
-    m->K.find_group(m->S, view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
+    m->K.find_group(m->S, view_of(m), fkeys, n, fidx, fmask, launch_of(m, st));
   else
     m->K.find(m->S, m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread,
-              view_of(m), keys, n, buf_indices, masks, launch_of(m, st));
+              view_of(m), fkeys, n, fidx, fmask, launch_of(m, st));
+  if (log_p > 0) partition_finish(m, pb, n, buf_indices, masks, st);
   return check_launch("find");
 }
 

@@ -37,7 +37,7 @@ const char* const kNames[kKernelKinds] = {
     "find", "insert_claim", "insert_commit", "erase_mark", "erase_resolve", "rebuild", "list_active",
     "heap_iota", "scatter_rows", "gather_rows", "gather_keys", "quantize", "probe_random_read", "set_ctrl",
     "batch_graph", "synth_keys", "find_neighbors", "gather_values", "depth_to_block_keys", "compact_new_keys",
-    "tsdf_integrate", "tsdf_raycast", "tsdf_ray_range"};
+    "tsdf_integrate", "tsdf_raycast", "tsdf_ray_range", "partition_keys", "unpermute_outputs"};
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {

@@ -29,6 +29,8 @@ enum KernelKind {
   kKIntegrate,
   kKRaycast,
   kKRayRange,
+  kKPartition,
+  kKUnpermute,
   kKernelKinds
 };
 

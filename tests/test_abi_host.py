@@ -30,7 +30,7 @@ def _err(status):
 def test_default_tuning_and_server_config():
     t = ash.default_tuning()
     assert (t.slots_per_bucket, t.keys_per_thread, t.find_keys_per_thread, t.warp_probe, t.auto_grow,
-            t.claim_mode, t.commit_keys_per_thread) == (4, 2, 1, 0, 1, 0, 1)
+            t.claim_mode, t.commit_keys_per_thread, t.partition_keys) == (4, 2, 1, 0, 1, 0, 1, 0)
     assert abs(t.slots_per_capacity - 2.0) < 1e-6 and abs(t.max_used_fraction - 0.65) < 1e-6
     c = ash.ash_server_default_config()
     assert (c.n_tenants, c.key_dim, c.zero_copy) == (16, 3, 0) and abs(c.max_load - 0.7) < 1e-6

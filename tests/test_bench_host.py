@@ -78,9 +78,11 @@ def test_byte_models_per_unit():
 def _full_result():
     """A result dict shaped like the GPU arm's, with every side block filled
     (sweep, per-op, batched, serving over five rates, TSDF, per-kernel)."""
-    point = {"n": 100_000_000, "rho": 0.5, "unique": 50_000_000, "working_set_x_l2": 36.3,
-             "activate": {"ms": 7.9, "keys_per_s": 1.27e10, "algo_gbs": 1510.3, "frac_hbm": 0.2251,
-                          "frac_random_access_roofline": 0.61234},
+    point = {"n": 100_000_000, "rho": 0.5, "unique": 50_000_000, "working_set_x_l2": 36.3, "ranged": True,
+             "activate": {"ms": 7.1, "keys_per_s": 1.4e10, "algo_gbs": 1680.3, "frac_hbm": 0.2461,
+                          "speedup_vs_input_order": 1.1123,
+                          "input_order": {"ms": 7.9, "keys_per_s": 1.27e10, "frac_hbm": 0.2251,
+                                          "frac_random_access_roofline": 0.61234}},
              "find": {"ms": 4.1, "keys_per_s": 2.43e10, "algo_gbs": 1970.1, "frac_hbm": 0.2937,
                       "frac_random_access_roofline": 0.7912}}
     rate = {m: {"p50_ms": 1.234567, "p99_ms": 7.654321, "p999_ms": 9.87, "req_per_s": 9512.25,
@@ -146,6 +148,11 @@ def test_summary_line_is_short_and_carries_the_contract(tmp_path, capsys):
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["config"]["workload"] == bench.WORKLOAD
     assert "served" in d["highlights"] and "sweep" in d["highlights"] and "batched_G" in d["highlights"]
+    # a ranged point reports its own rate and copy-peak fraction, and the
+    # input-order calls' roofline fraction and rate beside them
+    act = d["highlights"]["sweep"]["act"]
+    assert act[1] == pytest.approx(0.2461, abs=1e-3) and act[2] == pytest.approx(0.6123, abs=1e-3)
+    assert act[3] == pytest.approx(12.7, abs=0.1)
     assert json.load(open(detail)) == full
 
 

@@ -49,6 +49,8 @@ def test_random_sequences(seed):
     # the claim protocol switches between calls (its own generator, so the
     # operation sequence of each seed does not depend on it)
     mode_rng = np.random.default_rng(9000 + seed)
+    # key order (input or home-bucket ranges) switches too, from its own generator
+    part_rng = np.random.default_rng(9700 + seed)
     for step in range(40):
         op = rng.choice(["insert", "activate", "find", "erase", "rehash", "reserve", "clear"],
                         p=[0.3, 0.15, 0.25, 0.2, 0.04, 0.03, 0.03])
@@ -59,6 +61,10 @@ def test_random_sequences(seed):
         if op in ("insert", "activate"):
             tt = hm.tuning()
             tt.claim_mode = int(mode_rng.integers(0, 3))
+            hm.set_tuning(tt)
+        if op in ("insert", "activate", "find"):
+            tt = hm.tuning()
+            tt.partition_keys = int(part_rng.integers(0, 3))
             hm.set_tuning(tt)
         if op == "insert":
             if vrow:

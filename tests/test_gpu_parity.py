@@ -442,7 +442,8 @@ def test_edge_cases():
 
 
 @pytest.mark.parametrize("field,value", [("claim_mode", 3), ("claim_mode", -1), ("commit_keys_per_thread", 3),
-                                         ("keys_per_thread", 0), ("find_keys_per_thread", 5)])
+                                         ("keys_per_thread", 0), ("find_keys_per_thread", 5),
+                                         ("partition_keys", 3), ("partition_keys", -1)])
 def test_tuning_validation(field, value):
     """Out-of-range tuning fields are refused at create and at set_tuning,
     and a refused set_tuning leaves the map's tuning as it was."""
@@ -734,6 +735,100 @@ def test_repeated_batches_near_capacity(two_streams):
     assert hm.capacity() == om.capacity()
     assert_same_map(hm, om)
     assert_heap_permutation(hm)
+
+
+@pytest.mark.parametrize("d", [1, 3, 5])
+def test_partitioned_keys_match_oracle(d):
+    """Calls whose keys are first put in home-bucket range order (forced,
+    16+ ranges) equal the oracle: activate into a fresh map, find of hits and
+    misses, activate over existing keys, erase, find again.  Each input row
+    keeps its own output; the lowest position of equal keys wins."""
+    rng = np.random.default_rng(31 + d)
+    hm = ash.HashMap(d, 120_000, tuning=tuning(partition_keys=2))
+    om = oracle.OracleMap(d, 120_000, [])
+    a = rng.integers(-40, 40, size=(150_001, d)).astype(np.int32)
+    gi, gm = hm.activate(dev(a))
+    oi, omask = om.activate(a)
+    assert_op_parity(hm, a, gi, gm, oi, omask)
+    q = rng.integers(-45, 45, size=(70_003, d)).astype(np.int32)
+    gi, gm = hm.find(dev(q))
+    oi, omask = om.find(q)
+    assert_op_parity(hm, q, gi, gm, oi, omask, check_distinct=False)
+    b = rng.integers(-50, 50, size=(90_017, d)).astype(np.int32)
+    gi, gm = hm.activate(dev(b))
+    oi, omask = om.activate(b)
+    assert_op_parity(hm, b, gi, gm, oi, omask)
+    er = b[rng.integers(0, len(b), size=30_000)]
+    assert np.array_equal(hm.erase(dev(er)).cpu().numpy(), om.erase(er))
+    gi, gm = hm.find(dev(q))
+    oi, omask = om.find(q)
+    assert_op_parity(hm, q, gi, gm, oi, omask, check_distinct=False)
+    assert_same_map(hm, om)
+    assert_heap_permutation(hm)
+
+
+@pytest.mark.parametrize("n", [1, 31, 32_767, 32_768, 32_769, 100_000])
+def test_partitioned_ragged_sizes(n):
+    """Ranged calls at sizes around one partition block (32768 keys): the
+    same masks as calls in input order, and each index names its key."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(-2**20, 2**20, size=(n, 3)).astype(np.int32)
+    keys[n // 2:] = keys[: n - n // 2]  # duplicates, later positions lose
+    outs = []
+    for part in (1, 2):
+        hm = ash.HashMap(3, n, tuning=tuning(partition_keys=part))
+        gi, gm = hm.activate(dev(keys))
+        fi, fm = hm.find(dev(keys))
+        om = oracle.OracleMap(3, n, [])
+        oi, omask = om.activate(keys)
+        assert_op_parity(hm, keys, gi, gm, oi, omask)
+        assert fm.all() and torch.equal(hm.key_buffer()[fi.long()].cpu(), torch.from_numpy(keys))
+        outs.append(gm.cpu())
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_partitioned_first_occurrence_heavy_duplicates():
+    """10^6 keys from 1000 distinct triples, ranged: exactly the first
+    occurrence of each key wins (Sec. 4.4.2's heavy-duplicate setting)."""
+    rng = np.random.default_rng(15)
+    distinct = rng.integers(-2**30, 2**30, size=(1000, 3)).astype(np.int32)
+    keys = distinct[rng.integers(0, 1000, size=1_000_000)]
+    hm = ash.HashMap(3, 1_000_000, tuning=tuning(partition_keys=2))
+    gi, gm = hm.activate(dev(keys))
+    _, first = np.unique(keys, axis=0, return_index=True)
+    want = np.zeros(len(keys), bool)
+    want[first] = True
+    assert np.array_equal(gm.cpu().numpy(), want)
+    assert hm.size() == 1000
+
+
+def test_partitioned_at_full_size():
+    """2x10^7 uniform keys at uniqueness 0.5 into capacity 2x10^7 (the
+    table, 320 MB, is more than twice L2, so the default tuning ranges the
+    keys): an activate, then a find in a fresh random order: one winner per
+    distinct key, the first occurrence; every key found at its winner's
+    index."""
+    from bench import device_uniform_keys
+    n = 20_000_000
+    keys = device_uniform_keys(n, 0.5, 3, torch.device("cuda", 0))
+    hm = ash.HashMap(3, n)
+    gi, gm = hm.activate(keys)
+    perm = torch.randperm(n, device=keys.device)
+    fi_p, fm_p = hm.find(keys[perm].contiguous())
+    fi = torch.empty_like(fi_p)
+    fm = torch.empty_like(fm_p)
+    fi[perm] = fi_p
+    fm[perm] = fm_p
+    assert bool(fm.all())
+    n_unique = torch.unique(keys, dim=0).shape[0]
+    assert int(gm.sum()) == n_unique == hm.size()
+    # the winner of each index is the lowest position holding its key
+    pos = torch.arange(n, device=keys.device)
+    first = torch.full((hm.capacity(),), n, dtype=torch.int64, device=keys.device)
+    first.scatter_reduce_(0, fi.long(), pos, reduce="amin")
+    assert torch.equal(gm, first[fi.long()] == pos)
+    assert torch.equal(gi[gm], fi[gm])
+    assert torch.equal(hm.key_buffer()[fi.long()], keys)
 
 
 def test_commit_snapshot_avoids_host_sync():
