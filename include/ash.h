@@ -111,15 +111,15 @@ typedef struct ash_tuning {
   int32_t partition_keys;     /* find, activate, and insert into a map without value buffers:
                                  1 = use the keys in input order; 2 = first put them in the order
                                  of their home buckets' ranges (a stable partition into ranges of
-                                 about L2/4 bytes of table each, 8 ranges at least), so that the
+                                 about L2/2 bytes of table each, 8 ranges at least), so that the
                                  kernels work on one range of the table (and of kB) at a time and
                                  find it in L2; the outputs come back in input order, and equal
                                  keys keep their input order (the first occurrence still wins);
                                  0 = 2 for calls of at least 2^20 keys on a table larger than twice
                                  L2, else 1 (a ranged find reads kB in range order only when the
-                                 inserts were ranged too, so both switch together).  Takes about 9 + 4d bytes of stream-ordered scratch per
-                                 key during the call; if that cannot be had the call uses input
-                                 order */
+                                 inserts were ranged too, so both switch together).  Takes about
+                                 9 + 4d bytes of stream-ordered scratch per key during the call;
+                                 if that cannot be had the call uses input order */
 } ash_tuning;
 
 /* Fills *out with the defaults. */

@@ -848,10 +848,10 @@ constexpr uint32_t kNoRange = 0xFFFFFFFFu;
 __device__ __forceinline__ uint32_t key_range(uint64_t h, int log_p) { return hi32(h) >> (32 - log_p); }
 
 // The kPartSteps key rows of one lane in warp w's part of a tile (local
-// positions 256 w + 32 j + lane) and their ranges (kNoRange past the tile).
+// positions 256 w + 32 j + lane); zeros past the tile.
 template <int D>
-__device__ __forceinline__ void load_tile_rows(const int32_t* __restrict__ keys, int64_t base, int tn, int log_p,
-                                               int32_t (&k)[kPartSteps][D], uint32_t (&r)[kPartSteps]) {
+__device__ __forceinline__ void load_tile_rows(const int32_t* __restrict__ keys, int64_t base, int tn,
+                                               int32_t (&k)[kPartSteps][D]) {
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -864,9 +864,22 @@ __device__ __forceinline__ void load_tile_rows(const int32_t* __restrict__ keys,
       for (int c = 0; c < D; ++c) k[j][c] = 0;
     }
   }
+}
+
+// Their ranges (kNoRange past the tile).
+template <int D>
+__device__ __forceinline__ void tile_ranges(const int32_t (&k)[kPartSteps][D], int tn, int log_p,
+                                            uint32_t (&r)[kPartSteps]) {
+  const int w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < kPartSteps; ++j)
     r[j] = w * 256 + j * 32 + lane < tn ? key_range(hash_key<D>(k[j]), log_p) : kNoRange;
+}
+
+// Keys in tile at `base` of a span ending at t1.
+__device__ __forceinline__ int tile_keys(int64_t base, int64_t t1) {
+  return t1 - base < kPartTile ? static_cast<int>(t1 - base) : kPartTile;
 }
 
 // counts[p * G + b]: keys of range p in block b's span.
@@ -878,21 +891,21 @@ __global__ void __launch_bounds__(256) partition_count_kernel(const int32_t* __r
   const int P = 1 << log_p;
   for (int p = threadIdx.x; p < P; p += blockDim.x) s_hist[p] = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * tiles_per_block * kPartTile;
   const int64_t t1 = t0 + static_cast<int64_t>(tiles_per_block) * kPartTile < n
                          ? t0 + static_cast<int64_t>(tiles_per_block) * kPartTile
                          : n;
+  // each tile's rows are loaded while the tile before is being counted
+  int32_t k[kPartSteps][D];
+  if (t0 < t1) load_tile_rows<D>(keys, t0, tile_keys(t0, t1), k);
   for (int64_t base = t0; base < t1; base += kPartTile) {
-    const int tn = t1 - base < kPartTile ? static_cast<int>(t1 - base) : kPartTile;
-    int32_t k[kPartSteps][D];
+    const int tn = tile_keys(base, t1);
     uint32_t r[kPartSteps];
-    load_tile_rows<D>(keys, base, tn, log_p, k, r);
+    tile_ranges<D>(k, tn, log_p, r);
+    if (base + kPartTile < t1) load_tile_rows<D>(keys, base + kPartTile, tile_keys(base + kPartTile, t1), k);
 #pragma unroll
-    for (int j = 0; j < kPartSteps; ++j) {
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, r[j]);
-      if (r[j] != kNoRange && lane == __ffs(peers) - 1) atomicAdd(&s_hist[r[j]], static_cast<uint32_t>(__popc(peers)));
-    }
+    for (int j = 0; j < kPartSteps; ++j)
+      if (r[j] != kNoRange) atomicAdd(&s_hist[r[j]], 1u);
   }
   __syncthreads();
   for (int p = threadIdx.x; p < P; p += blockDim.x) counts[static_cast<int64_t>(p) * gridDim.x + blockIdx.x] = s_hist[p];
@@ -939,12 +952,13 @@ __global__ void __launch_bounds__(256) partition_scatter_kernel(const int32_t* _
                          ? t0 + static_cast<int64_t>(tiles_per_block) * kPartTile
                          : n;
   for (int64_t base = t0; base < t1; base += kPartTile) {
-    const int tn = t1 - base < kPartTile ? static_cast<int>(t1 - base) : kPartTile;
+    const int tn = tile_keys(base, t1);
     for (int p = lane; p < P; p += 32) s_cnt[w][p] = 0u;
     __syncwarp();
     int32_t k[kPartSteps][D];
     uint32_t r[kPartSteps];
-    load_tile_rows<D>(keys, base, tn, log_p, k, r);
+    load_tile_rows<D>(keys, base, tn, k);
+    tile_ranges<D>(k, tn, log_p, r);
     uint32_t rank[kPartSteps];
 #pragma unroll
     for (int j = 0; j < kPartSteps; ++j) {

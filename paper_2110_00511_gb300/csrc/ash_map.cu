@@ -244,15 +244,17 @@ int claim_prefers_slot(const ash_map* m) {
 }
 
 // log2 of the number of home-bucket ranges a call on n keys is partitioned
-// into, 0 for input order (tuning.partition_keys): ranges of at most L2/4
-// bytes of table, 2 to 256 of them (8 at least when forced).  By default,
-// calls of 2^20 keys or more on a table larger than twice L2.  The pay-off
-// needs both sides: a ranged find reads kB in range order only if the
-// inserts handed out indices in range order too.  Measured on GB300
-// (uniform keys, uniqueness 0.5, capacity n, queries in a fresh random
-// order), ranged against input order: at 2x10^7 keys activate 1.19 / 1.21 ms
-// and find 0.57 / 0.81 ms; at 10^8 activate 7.5 / 8.0 ms and find 4.6 /
-// 5.2 ms; at 10^7 (table 1.2x L2) activate 0.54-0.59 / 0.53 ms.
+// into, 0 for input order (tuning.partition_keys): 2 to 256 ranges of at
+// most L2/2 bytes of table (8 at least when forced).  By default, calls of
+// 2^20 keys or more on a table larger than twice L2.  The pay-off needs
+// both sides: a ranged find reads kB in range order only if the inserts
+// handed out indices in the same ranges.  Measured on GB300 (uniform keys,
+// uniqueness 0.5, capacity n, queries in a fresh random order), ranged
+// against input order: at 10^8 keys activate 6.6 / 8.0 ms and find 4.5 /
+// 5.2 ms; at 2x10^7 activate 1.12 / 1.22 ms and find 0.57 / 0.81 ms; at
+// 10^7 keys (table 1.2x L2) a ranged activate took 0.59 against 0.53 ms.
+// Ranges of L2/4 gave activate 6.9-7.2 and find 4.2 ms at 10^8; L2/4 for
+// finds after L2/2 inserts, find 4.5 ms.
 int partition_log(const ash_map* m, int64_t n) {
   const int mode = m->tuning.partition_keys;
   if (mode == 1 || n <= 0) return 0;
@@ -260,7 +262,7 @@ int partition_log(const ash_map* m, int64_t n) {
   const int64_t l2 = l2_bytes(m->device);
   if (mode == 0 && (table <= 2 * l2 || n < (int64_t{1} << 20))) return 0;
   int lg = 1;
-  while (lg < ash::kPartMaxLog && (table >> lg) > l2 / 4) ++lg;
+  while (lg < ash::kPartMaxLog && (table >> lg) > l2 / 2) ++lg;
   return mode == 2 ? std::max(lg, 3) : lg;
 }
 
