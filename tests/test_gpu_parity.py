@@ -802,6 +802,64 @@ def test_partitioned_first_occurrence_heavy_duplicates():
     assert hm.size() == 1000
 
 
+_REFUSING_ALLOCATOR = []  # the callbacks outlive every map that uses them
+
+
+def test_partitioned_call_without_scratch_uses_input_order():
+    """A ranged call whose stream-ordered scratch cannot be had (the map's
+    allocator refuses it) runs its keys in input order instead, with the
+    same results: activate and find against the oracle."""
+    import ctypes
+    refuse = {"above": None}
+
+    def _alloc(nbytes, device, stream, ctx):
+        if refuse["above"] is not None and nbytes > refuse["above"]:
+            return 0
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:
+            return 0
+
+    def _free(ptr, device, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ash._ALLOC_FN(_alloc), ash._FREE_FN(_free)
+    _REFUSING_ALLOCATOR.extend([a, f, refuse])
+    L = ash.lib()
+    ash._check(L.ash_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+    try:
+        hm = ash.HashMap(3, 150_001, tuning=tuning(partition_keys=2))
+    finally:
+        ash._check(L.ash_set_allocator(None, None, None))  # maps keep the allocator they were created with
+    rng = np.random.default_rng(41)
+    keys = rng.integers(-30, 30, size=(150_001, 3)).astype(np.int32)
+    kd = dev(keys)
+
+    def partition_launches(fn):  # (fn's result, traced partitions)
+        ash.ash_trace_reset()
+        ash.ash_trace_enable(True)
+        out = fn()
+        torch.cuda.synchronize()
+        ash.ash_trace_enable(False)
+        return out, ash.ash_trace_collect()["partition_keys"][1]
+
+    refuse["above"] = 1 << 20  # the call's scratch is about 3 MB
+    (gi, gm), n_act = partition_launches(lambda: hm.activate(kd))
+    (fi, fm), n_find = partition_launches(lambda: hm.find(kd))
+    refuse["above"] = None
+    assert n_act == 0 and n_find == 0, "a call whose scratch was refused still partitioned"
+    om = oracle.OracleMap(3, 150_001, [])
+    oi, omask = om.activate(keys)
+    assert_op_parity(hm, keys, gi, gm, oi, omask)
+    assert bool(fm.all()) and torch.equal(hm.key_buffer()[fi.long()].cpu(), torch.from_numpy(keys))
+    # with the scratch available the same find is ranged (one traced
+    # partition: count, scan, scatter)
+    (fi2, fm2), n_find2 = partition_launches(lambda: hm.find(kd))
+    assert n_find2 == 1 and torch.equal(fi2, fi) and torch.equal(fm2, fm)
+    assert_same_map(hm, om)
+    del hm
+
+
 def test_partitioned_at_full_size():
     """2x10^7 uniform keys at uniqueness 0.5 into capacity 2x10^7 (the
     table, 320 MB, is more than twice L2, so the default tuning ranges the
