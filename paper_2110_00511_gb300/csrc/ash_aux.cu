@@ -47,6 +47,23 @@ void launch_partition_scan(uint32_t* counts, int G, int P, uint32_t* range_total
   launch_dependent(partition_scan_kernel, P, 256, L.stream, counts, G, range_totals);
 }
 
+// Asks the L2 to fetch [base, base + bytes) (one prefetch per 128-byte
+// line); the loads that follow find the lines there instead of missing at
+// random.  A hint: nothing waits for it.
+__global__ void __launch_bounds__(256) prefetch_l2_kernel(const char* __restrict__ base, int64_t bytes) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * 128;
+  for (int64_t off = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 128; off < bytes; off += stride)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+}
+
+void launch_prefetch_l2(const void* base, int64_t bytes, const Launch& L) {
+  if (bytes <= 0) return;
+  const int64_t lines = (bytes + 127) / 128;
+  const int64_t want = (lines + 255) / 256;
+  const int grid = static_cast<int>(want < L.grid_cap ? (want < 1 ? 1 : want) : L.grid_cap);
+  prefetch_l2_kernel<<<grid, 256, 0, L.stream>>>(static_cast<const char*>(base), bytes);
+}
+
 // Four positions per thread: the dest loads, then the gathers, then the
 // stores.  A gather follows one of P runs that each advance in order.
 __global__ void __launch_bounds__(256) unpermute_kernel(const int32_t* __restrict__ dest, int64_t n,

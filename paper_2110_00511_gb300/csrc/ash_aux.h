@@ -22,6 +22,9 @@ void launch_list_active(bool heap_identity, const int32_t* heap, int64_t capacit
                         int32_t* out, int64_t out_cap, long long* count_out, const Launch& L);
 void launch_set_top_used(Ctrl* ctrl, int64_t top, int64_t used, const Launch& L);
 void launch_set_used_from_count(Ctrl* ctrl, const Launch& L);
+// L2 prefetch of a byte range (a hint; plain stream order, no programmatic
+// overlap, so it never runs beside the kernel before it).
+void launch_prefetch_l2(const void* base, int64_t bytes, const Launch& L);
 // Publishes the control block to a host-visible snapshot (publish_snapshot).
 void launch_snapshot(Ctrl* ctrl, Snap* snap, uint32_t seq, const Launch& L);
 void launch_iota(int32_t* h, int64_t from, int64_t to, const Launch& L);

@@ -297,6 +297,15 @@ bool partition_call(ash_map* m, const int32_t* keys, int64_t n, int log_p, cudaS
   return true;
 }
 
+// The table buckets of range p of P (and a bucket past it, for probes
+// that run on), asked into L2 before the range's keys are worked on.
+void prefetch_table_range(const ash_map* m, int p, int P, const ash::Launch& L) {
+  const int64_t b0 = static_cast<int64_t>(m->n_buckets) * p / P;
+  int64_t b1 = static_cast<int64_t>(m->n_buckets) * (p + 1) / P + 1;
+  if (b1 > m->n_buckets) b1 = m->n_buckets;
+  ash::launch_prefetch_l2(m->slots + b0 * m->S, (b1 - b0) * m->S * 8, L);
+}
+
 // The partitioned call's outputs back in input order; its scratch freed.
 void partition_finish(ash_map* m, const PartBufs& pb, int64_t n, int32_t* idx, uint8_t* mask, cudaStream_t st) {
   ash::launch_unpermute(pb.dest, n, pb.idx, pb.mask, idx, mask, launch_of(m, st));
@@ -842,6 +851,25 @@ ash_status insert_impl(ash_map* m, const int32_t* keys, const void* const* value
   if (pts) {
     m->K.claim_pts(m->S, kpt, pref, tv, *pts, n, idx, L);
     m->K.commit_pts(ckpt, tv, *pts, n, idx, mask, inline_value ? &vr : nullptr, L);
+  } else if (log_p > 0) {
+    // One range after the other: its table buckets are asked into L2, then
+    // its keys claimed and committed.  The slices are the ranged order cut
+    // at n p / P (about the ranges' bounds, which only the device knows).
+    // Cutting claims and commits by position keeps the results: a slice's
+    // keys equal to a key committed by an earlier slice report it present,
+    // as losers of a join would, and the lowest position wins either way.
+    const int P = 1 << log_p;
+    for (int p = 0; p < P; ++p) {
+      const int64_t a = n * p / P;
+      const int64_t b = n * (p + 1) / P;  // the last slice is never empty
+      if (b == a) continue;
+      prefetch_table_range(m, p, P, L);
+      ash::TableView tvp = tv;
+      if (p != P - 1) tvp.snap = nullptr;  // the last commit publishes the control block
+      const int32_t* sk = ckeys + a * m->key_dim;
+      m->K.claim(m->S, kpt, pref, tvp, sk, b - a, cidx + a, L);
+      m->K.commit(ckpt, tvp, sk, b - a, cidx + a, cmask + a, inline_value ? &vr : nullptr, L);
+    }
   } else {
     m->K.claim(m->S, kpt, pref, tv, ckeys, n, cidx, L);
     m->K.commit(ckpt, tv, ckeys, n, cidx, cmask, inline_value ? &vr : nullptr, L);
@@ -999,11 +1027,22 @@ ash_status ash_find(ash_map* m, const int32_t* keys, int64_t n, int32_t* buf_ind
   const int32_t* fkeys = log_p > 0 ? pb.keys : keys;
   int32_t* fidx = log_p > 0 ? pb.idx : buf_indices;
   uint8_t* fmask = log_p > 0 ? pb.mask : masks;
-  if (m->tuning.warp_probe == 1)
-    m->K.find_group(m->S, view_of(m), fkeys, n, fidx, fmask, launch_of(m, st));
-  else
-    m->K.find(m->S, m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread,
-              view_of(m), fkeys, n, fidx, fmask, launch_of(m, st));
+  const ash::Launch L = launch_of(m, st);
+  const int fkpt = m->tuning.find_keys_per_thread ? m->tuning.find_keys_per_thread : m->tuning.keys_per_thread;
+  const int P = log_p > 0 ? 1 << log_p : 1;
+  for (int p = 0; p < P; ++p) {
+    // ranged: one range after the other, its table buckets asked into L2
+    // first (slices cut at n p / P, as for inserts)
+    const int64_t a = n * p / P;
+    const int64_t b = n * (p + 1) / P;
+    if (b == a) continue;
+    if (log_p > 0) prefetch_table_range(m, p, P, L);
+    const int32_t* sk = fkeys + a * m->key_dim;
+    if (m->tuning.warp_probe == 1)
+      m->K.find_group(m->S, view_of(m), sk, b - a, fidx + a, fmask + a, L);
+    else
+      m->K.find(m->S, fkpt, view_of(m), sk, b - a, fidx + a, fmask + a, L);
+  }
   if (log_p > 0) partition_finish(m, pb, n, buf_indices, masks, st);
   return check_launch("find");
 }
