@@ -250,11 +250,11 @@ int claim_prefers_slot(const ash_map* m) {
 // both sides: a ranged find reads kB in range order only if the inserts
 // handed out indices in the same ranges.  Measured on GB300 (uniform keys,
 // uniqueness 0.5, capacity n, queries in a fresh random order), ranged
-// against input order: at 10^8 keys activate 6.6 / 8.0 ms and find 4.5 /
-// 5.2 ms; at 2x10^7 activate 1.12 / 1.22 ms and find 0.57 / 0.81 ms; at
-// 10^7 keys (table 1.2x L2) a ranged activate took 0.59 against 0.53 ms.
-// Ranges of L2/4 gave activate 6.9-7.2 and find 4.2 ms at 10^8; L2/4 for
-// finds after L2/2 inserts, find 4.5 ms.
+// against input order: at 10^8 keys activate 5.6 / 7.9 ms and find 3.1 /
+// 5.1 ms; at 2x10^7 activate 1.12 / 1.23 ms and find 0.58 / 0.80 ms.  Before
+// the calls worked range by range (one launch over all ranged keys), a
+// ranged activate of 10^7 keys (table 1.2x L2) took 0.59 against 0.53 ms,
+// and ranges of L2/4 ran level with L2/2 at 10^8.
 int partition_log(const ash_map* m, int64_t n) {
   const int mode = m->tuning.partition_keys;
   if (mode == 1 || n <= 0) return 0;
