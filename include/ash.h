@@ -111,9 +111,10 @@ typedef struct ash_tuning {
   int32_t partition_keys;     /* find, activate, and insert into a map without value buffers:
                                  1 = use the keys in input order; 2 = first put them in the order
                                  of their home buckets' ranges (a stable partition into ranges of
-                                 about L2/2 bytes of table each, 8 ranges at least), so that the
-                                 kernels work on one range of the table (and of kB) at a time and
-                                 find it in L2; the outputs come back in input order, and equal
+                                 about L2/2 bytes of table each, 8 ranges at least) and work range
+                                 by range, each range's table buckets prefetched into L2 before its
+                                 keys, so that the kernels find the table (and kB) in L2 instead of
+                                 missing at random; the outputs come back in input order, and equal
                                  keys keep their input order (the first occurrence still wins);
                                  0 = 2 for calls of at least 2^20 keys on a table larger than twice
                                  L2, else 1 (a ranged find reads kB in range order only when the
