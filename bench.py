@@ -462,7 +462,7 @@ def cpu_baseline_tsdf_frame(c):
 
 
 # ------------------------------------------------------------ output line
-COMPACT_LIMIT = 1450  # bytes of the one stdout line
+COMPACT_LIMIT = 1600  # bytes of the one stdout line (well under the 2 KB a log tail keeps)
 
 
 def _sig(x, digits=4):
